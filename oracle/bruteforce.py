@@ -1,0 +1,143 @@
+"""Brute-force rounding checker (pure Python, exact rationals).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  This module pins the C
+oracle: it shares no code or formula with it.  Instead of integer arithmetic on
+significands it
+
+1. lists every finite value of a small format ``1/E/M`` as an exact
+   ``fractions.Fraction``, sorted;
+2. forms the exact result of ``x + y`` or ``x * y`` as a Fraction;
+3. finds the correctly rounded neighbour by binary search in that list:
+   round to nearest with ties to the neighbour whose encoding is even, or
+   round toward zero (the two modes of the paper's Sec. 4), with IEEE-754
+   overflow (RN: to infinity once the magnitude reaches max + half an ulp;
+   RZ: to the largest finite value) and IEEE signed zeros.
+
+Only practical for formats of up to about 12 bits.
+"""
+from __future__ import annotations
+
+import bisect
+from fractions import Fraction
+from functools import lru_cache
+
+RN, RZ = 0, 1
+
+
+class Format:
+    def __init__(self, E: int, M: int):
+        self.E, self.M = E, M
+        self.B = 1 + E + M
+        self.bias = 2 ** (E - 1) - 1
+        self.emax = 2 ** E - 1
+        # all non-negative finite encodings, in increasing value order
+        self.pos_codes = [(e << M) | f for e in range(self.emax) for f in range(2 ** M)]
+        self.pos_vals = [self.value(c) for c in self.pos_codes]
+        assert all(a < b for a, b in zip(self.pos_vals, self.pos_vals[1:]))
+        self.max_finite = self.pos_vals[-1]
+        # the rounding boundary to infinity in RN: max + half an ulp of the top binade
+        top_ulp = Fraction(2) ** (self.emax - 1 - self.bias - M)
+        self.ovf_rn = self.max_finite + top_ulp / 2
+        self.nan = (self.emax << M) | (1 << (M - 1))
+        self.sign_bit = 1 << (E + M)
+
+    # -- decoding ---------------------------------------------------------------
+    def fields(self, code: int):
+        M, E = self.M, self.E
+        return (code >> (E + M)) & 1, (code >> M) & (2 ** E - 1), code & (2 ** M - 1)
+
+    def value(self, code: int) -> Fraction:
+        """Exact value of a finite encoding (IEEE-754 style reading)."""
+        s, e, f = self.fields(code)
+        assert e != self.emax
+        if e == 0:
+            v = Fraction(f, 2 ** self.M) * Fraction(2) ** (1 - self.bias)
+        else:
+            v = (1 + Fraction(f, 2 ** self.M)) * Fraction(2) ** (e - self.bias)
+        return -v if s else v
+
+    def is_nan(self, code):
+        _, e, f = self.fields(code)
+        return e == self.emax and f != 0
+
+    def is_inf(self, code):
+        _, e, f = self.fields(code)
+        return e == self.emax and f == 0
+
+    def inf(self, s):
+        return (s << (self.E + self.M)) | (self.emax << self.M)
+
+    # -- rounding ---------------------------------------------------------------
+    def round(self, v: Fraction, rnd: int) -> int:
+        """Correctly rounded encoding of a nonzero exact value."""
+        assert v != 0
+        s = 1 if v < 0 else 0
+        a = -v if s else v
+        sgn = s * self.sign_bit
+        if rnd == RN:
+            if a >= self.ovf_rn:
+                return self.inf(s)
+        else:
+            if a > self.max_finite:
+                return sgn | self.pos_codes[-1]
+        vals = self.pos_vals
+        i = bisect.bisect_right(vals, a) - 1      # vals[i] <= a
+        if vals[i] == a:
+            return sgn | self.pos_codes[i]
+        if rnd == RZ:
+            return sgn | self.pos_codes[i]
+        lo, hi = vals[i], vals[i + 1] if i + 1 < len(vals) else None
+        if hi is None:                            # between max and the RN boundary
+            return sgn | self.pos_codes[i]
+        dl, dh = a - lo, hi - a
+        if dl < dh:
+            return sgn | self.pos_codes[i]
+        if dh < dl:
+            return sgn | self.pos_codes[i + 1]
+        # tie: the neighbour with an even encoding
+        return sgn | (self.pos_codes[i] if self.pos_codes[i] % 2 == 0 else self.pos_codes[i + 1])
+
+    # -- operations ---------------------------------------------------------------
+    def add(self, x: int, y: int, rnd: int) -> int:
+        if self.is_nan(x) or self.is_nan(y):
+            return self.nan
+        sx, sy = self.fields(x)[0], self.fields(y)[0]
+        if self.is_inf(x) and self.is_inf(y):
+            return self.inf(sx) if sx == sy else self.nan
+        if self.is_inf(x):
+            return self.inf(sx)
+        if self.is_inf(y):
+            return self.inf(sy)
+        v = self.value(x) + self.value(y)
+        if v == 0:
+            # exact zero: -0 only for (-0) + (-0); otherwise +0 (RN and RZ)
+            return self.sign_bit if (sx and sy) else 0
+        return self.round(v, rnd)
+
+    def sub(self, x: int, y: int, rnd: int) -> int:
+        return self.add(x, y ^ self.sign_bit, rnd)
+
+    def mul(self, x: int, y: int, rnd: int) -> int:
+        if self.is_nan(x) or self.is_nan(y):
+            return self.nan
+        sx, sy = self.fields(x)[0], self.fields(y)[0]
+        s = sx ^ sy
+        if self.is_inf(x) or self.is_inf(y):
+            other = y if self.is_inf(x) else x
+            if not self.is_inf(other) and self.value(other) == 0:
+                return self.nan
+            return self.inf(s)
+        v = self.value(x) * self.value(y)
+        if v == 0:
+            return s * self.sign_bit
+        r = self.round(v, rnd)
+        # a nonzero product that rounds to zero keeps the sign of the exact result
+        return r
+
+    def fma2(self, x: int, y: int, z: int, rnd: int) -> int:
+        return self.add(self.mul(x, y, rnd), z, rnd)
+
+
+@lru_cache(maxsize=None)
+def fmt(E: int, M: int) -> Format:
+    return Format(E, M)

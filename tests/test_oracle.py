@@ -1,0 +1,343 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle (``oracle/bsfp_oracle.c``) is checked against things that do not
+depend on it:
+
+* the brute-force Fraction checker (``oracle/bruteforce.py``), exhaustively
+  over every operand pair of small formats (add, sub, mul; RN and RZ);
+* hand-derived values in ``tests/golden/`` (Sec. 5.2's 1/4/3 format, Sec. 2's
+  Fig. 1 layout);
+* the host FPU: IEEE binary16 through numpy (1/5/10, the paper's FP16),
+  binary32 through C ``fesetround`` (1/8/23, the paper's FP32), bfloat16 through
+  torch (1/8/7);
+* a neighbour check of correct rounding for every sweep format
+  (E 3..8 x M 2..23): the result's encoding neighbours bracket the exact value
+  as RN-even / RZ require;
+* algebraic invariants.
+"""
+from __future__ import annotations
+
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import bruteforce as bf
+from tests import _helpers as H
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RND = {"rn": oracle.RN, "rz": oracle.RZ}
+
+SMALL_FORMATS = [(2, 1), (2, 3), (3, 2), (3, 3), (2, 5), (3, 4), (4, 3), (5, 2)]
+
+
+# ---------------------------------------------------------------------------
+# brute force, exhaustive
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("E,M", SMALL_FORMATS)
+@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_exhaustive_vs_bruteforce(E, M, op, rnd):
+    F = bf.fmt(E, M)
+    a, b = synth.all_pairs(F.B)
+    got = oracle.binop(op, E, M, rnd, a, b)
+    fn = getattr(F, op)
+    want = np.fromiter((fn(int(x), int(y), rnd) for x, y in zip(a, b)), dtype=np.uint32,
+                       count=a.size)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, "first mismatch a=%#x b=%#x oracle=%#x brute=%#x" % (
+        a[bad[0]], b[bad[0]], got[bad[0]], want[bad[0]])
+
+
+@pytest.mark.parametrize("E,M", [(4, 3), (3, 3), (4, 4)])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_fma2_vs_bruteforce_sampled(E, M, rnd):
+    F = bf.fmt(E, M)
+    n = 6000
+    a = synth.uniform_bits(F.B, n, 11, 0)
+    b = synth.uniform_bits(F.B, n, 11, 1)
+    c = synth.uniform_bits(F.B, n, 11, 2)
+    got = oracle.fma2(E, M, rnd, a, b, c)
+    want = np.array([F.fma2(int(x), int(y), int(z), rnd) for x, y, z in zip(a, b, c)],
+                    dtype=np.uint32)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("E,M", [(4, 4), (5, 4), (4, 5)])
+def test_nine_and_ten_bit_vs_bruteforce_sampled(E, M):
+    F = bf.fmt(E, M)
+    n = 20000
+    a = synth.fp_values(E, M, n, 5, 0)
+    b = synth.fp_values(E, M, n, 5, 1)
+    for rnd in (oracle.RN, oracle.RZ):
+        for op in ("add", "mul"):
+            got = oracle.binop(op, E, M, rnd, a, b)
+            fn = getattr(F, op)
+            want = np.array([fn(int(x), int(y), rnd) for x, y in zip(a, b)], dtype=np.uint32)
+            assert np.array_equal(got, want), (op, rnd)
+
+
+# ---------------------------------------------------------------------------
+# hand-derived golden values
+# ---------------------------------------------------------------------------
+def _golden_arith():
+    rows = []
+    with open(os.path.join(GOLDEN, "arith_1_4_3.txt")) as fh:
+        for line in fh:
+            body = line.split("#")[0].strip()
+            if not body:
+                continue
+            lhs, exp = body.split("->")
+            toks = lhs.split()
+            rows.append((toks[0], RND[toks[1]], [int(t, 16) for t in toks[2:]], int(exp, 16),
+                         line.strip()))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_arith(), ids=lambda r: r[4].split("#")[0].strip())
+def test_golden_arith_1_4_3(row):
+    op, rnd, args, want, _ = row
+    vals = [np.array([v], dtype=np.uint32) for v in args]
+    got = int(oracle.binop(op, 4, 3, rnd, *vals)[0])
+    assert got == want, "%s: got %#x" % (row[4], got)
+
+
+def _golden_layout():
+    cases, cur = [], None
+    with open(os.path.join(GOLDEN, "fig1_layout_1_4_3.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, rest = line.split(None, 1)
+            if key == "case":
+                cur = {"name": rest}
+                cases.append(cur)
+            elif key == "elems":
+                cur["elems"] = [int(t, 16) for t in rest.split()]
+            elif key == "words":
+                cur["words"] = [int(t, 16) for t in rest.split()]
+    return cases
+
+
+@pytest.mark.parametrize("case", _golden_layout(), ids=lambda c: c["name"])
+def test_golden_fig1_layout(case):
+    x = np.array(case["elems"], dtype=np.uint32)
+    planes = oracle.pack(8, x)
+    assert planes.shape == (8, oracle.plane_stride(16))
+    assert [int(w) for w in planes[:, 0]] == case["words"]
+    assert not planes[:, 1:].any()          # padding words are zero
+    assert np.array_equal(oracle.unpack(8, planes, 16), x)
+
+
+# ---------------------------------------------------------------------------
+# pack / unpack properties
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("B,n", [(8, 1), (9, 31), (13, 32), (13, 33), (16, 1023), (32, 1025), (6, 4097)])
+def test_pack_roundtrip_and_counts(B, n):
+    x = synth.uniform_bits(B, n, 3).astype(np.uint32)
+    planes = oracle.pack(B, x)
+    S = oracle.plane_stride(n)
+    assert S % 32 == 0 and S * 32 >= n
+    assert np.array_equal(oracle.unpack(B, planes, n), x)
+    # plane b holds exactly the elements whose bit b is set (popcount check)
+    for b in range(B):
+        ones = sum(bin(int(w)).count("1") for w in planes[b])
+        assert ones == int(((x >> b) & 1).sum())
+    # lanes past n are zero
+    last = n // 32
+    if n % 32:
+        assert not (planes[:, last] >> (n % 32)).any()
+    assert not planes[:, (n + 31) // 32:].any()
+
+
+# ---------------------------------------------------------------------------
+# host IEEE pins
+# ---------------------------------------------------------------------------
+def _f16_specials():
+    v = [0x0000, 0x8000, 0x0001, 0x8001, 0x03FF, 0x0400, 0x83FF, 0x3C00, 0xBC00, 0x7BFF, 0xFBFF,
+         0x7C00, 0xFC00, 0x7E00, 0x7C01, 0x3BFF, 0x3C01, 0x4000, 0x0200, 0x1400, 0x5BFF]
+    a = np.repeat(np.array(v, np.uint32), len(v))
+    b = np.tile(np.array(v, np.uint32), len(v))
+    return a, b
+
+
+def _f16_operands():
+    n = 1 << 17
+    a1 = synth.uniform_bits(16, n, 21, 0).astype(np.uint32)
+    b1 = synth.uniform_bits(16, n, 21, 1).astype(np.uint32)
+    a2 = synth.fp_values(5, 10, n, 22, 0).astype(np.uint32)
+    b2 = synth.fp_values(5, 10, n, 22, 1).astype(np.uint32)
+    # nearby exponents, so that cancellation and ties happen often
+    a3 = a2.copy()
+    b3 = (a2 ^ synth.uniform_bits(6, n, 23).astype(np.uint32)) ^ 0x8000
+    sa, sb = _f16_specials()
+    return np.concatenate([a1, a2, a3, sa]), np.concatenate([b1, b2, b3, sb])
+
+
+@pytest.mark.parametrize("op", ["add", "mul"])
+def test_binary16_rn_vs_numpy(op):
+    a, b = _f16_operands()
+    fa = a.astype(np.uint16).view(np.float16)
+    fb = b.astype(np.uint16).view(np.float16)
+    with np.errstate(all="ignore"):
+        ref = (fa + fb) if op == "add" else (fa * fb)
+    want = ref.view(np.uint16).astype(np.uint32)
+    got = oracle.binop(op, 5, 10, oracle.RN, a, b)
+    ok = H.nan_class_equal(5, 10, got, want)
+    assert ok.all(), "first mismatch %#x %#x" % (a[~ok][0], b[~ok][0])
+
+
+@pytest.mark.parametrize("op", ["add", "mul"])
+def test_binary16_rz_vs_exact_double(op):
+    """binary16 sums and products are exact in binary64; truncating that exact
+    value toward zero is the RZ result."""
+    a, b = _f16_operands()
+    fa = a.astype(np.uint16).view(np.float16).astype(np.float64)
+    fb = b.astype(np.uint16).view(np.float16).astype(np.float64)
+    with np.errstate(all="ignore"):
+        ex = (fa + fb) if op == "add" else (fa * fb)
+        r = ex.astype(np.float16)                          # correctly rounded (RN)
+        over = np.abs(r.astype(np.float64)) > np.abs(ex)   # RN went away from zero
+        r = np.where(over, np.nextafter(r, np.float16(0)), r)
+    want = r.view(np.uint16).astype(np.uint32)
+    # exact zero results: +0 except (-0)+(-0); numpy already follows IEEE here
+    got = oracle.binop(op, 5, 10, oracle.RZ, a, b)
+    ok = H.nan_class_equal(5, 10, got, want)
+    assert ok.all(), "first mismatch %#x %#x got %#x want %#x" % (
+        a[~ok][0], b[~ok][0], got[~ok][0], want[~ok][0])
+
+
+@pytest.mark.parametrize("op", ["add", "mul"])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_binary32_vs_host_fenv(op, rnd):
+    n = 1 << 17
+    a = np.concatenate([synth.splitmix64(31, n, 0).astype(np.uint32),
+                        synth.fp_values(8, 23, n, 32, 0).astype(np.uint32)])
+    b = np.concatenate([synth.splitmix64(31, n, 1).astype(np.uint32),
+                        synth.fp_values(8, 23, n, 32, 1).astype(np.uint32)])
+    # near-cancellation pairs
+    b2 = (a[n:] ^ 0x80000000) ^ (synth.splitmix64(33, n).astype(np.uint32) & 0x3FF)
+    a = np.concatenate([a, a[n:]])
+    b = np.concatenate([b, b2])
+    want = H.host_f32(op, rnd, a, b)
+    got = oracle.binop(op, 8, 23, rnd, a, b)
+    ok = H.nan_class_equal(8, 23, got, want)
+    assert ok.all(), "first mismatch %#x %#x got %#x want %#x" % (
+        a[~ok][0], b[~ok][0], got[~ok][0], want[~ok][0])
+
+
+def test_bfloat16_rn_vs_torch():
+    torch = pytest.importorskip("torch")
+    # subnormal behaviour of torch's CPU bfloat16 first (2^-133 + 2^-133 = 2^-132)
+    tiny = torch.tensor([0x0001], dtype=torch.int16).view(torch.bfloat16)
+    assert int((tiny + tiny).view(torch.int16)) == 0x0002
+    n = 1 << 17
+    a = np.concatenate([synth.uniform_bits(16, n, 41, 0), synth.fp_values(8, 7, n, 42, 0)]).astype(np.uint32)
+    b = np.concatenate([synth.uniform_bits(16, n, 41, 1), synth.fp_values(8, 7, n, 42, 1)]).astype(np.uint32)
+    ta = torch.from_numpy(a.astype(np.int32).astype(np.int16)).view(torch.bfloat16)
+    tb = torch.from_numpy(b.astype(np.int32).astype(np.int16)).view(torch.bfloat16)
+    for op in ("add", "mul"):
+        r = (ta + tb) if op == "add" else (ta * tb)
+        want = r.view(torch.int16).numpy().astype(np.uint16).astype(np.uint32)
+        got = oracle.binop(op, 8, 7, oracle.RN, a, b)
+        ok = H.nan_class_equal(8, 7, got, want)
+        assert ok.all(), (op, hex(a[~ok][0]), hex(b[~ok][0]))
+
+
+# ---------------------------------------------------------------------------
+# neighbour check of correct rounding, every sweep format
+# ---------------------------------------------------------------------------
+def _check_rounding(E, M, rnd, v: Fraction, r: int):
+    """Assert that encoding r is the RN-even / RZ rounding of nonzero exact v."""
+    bias = (1 << (E - 1)) - 1
+    emax = (1 << E) - 1
+    sign_bit = 1 << (E + M)
+    mag = r & (sign_bit - 1)
+    s = 1 if v < 0 else 0
+    a = -v if s else v
+    assert (r >> (E + M)) & 1 == s, "sign"
+    inf_code = emax << M
+    maxf = H.value(E, M, inf_code - 1)
+    ovf = maxf + Fraction(2) ** (emax - 1 - bias - M) / 2
+    if rnd == oracle.RZ:
+        if a > maxf:
+            assert mag == inf_code - 1
+            return
+        assert mag < inf_code
+        lo = H.value(E, M, mag)
+        assert lo <= a < H.value(E, M, mag + 1) if mag + 1 < inf_code else lo <= a
+        return
+    if mag == inf_code:
+        assert a >= ovf
+        return
+    assert mag < inf_code
+    x = H.value(E, M, mag)
+    if mag > 0:
+        lo_mid = (H.value(E, M, mag - 1) + x) / 2
+        assert a >= lo_mid and (a != lo_mid or mag % 2 == 0)
+    hi_mid = (x + H.value(E, M, mag + 1)) / 2 if mag + 1 < inf_code else ovf
+    assert a <= hi_mid and (a != hi_mid or mag % 2 == 0)
+
+
+SWEEP = [(E, M) for E in range(3, 9) for M in range(2, 24)]
+
+
+@pytest.mark.parametrize("E", range(3, 9))
+def test_sweep_formats_correct_rounding(E):
+    n = 120
+    for M in range(2, 24):
+        a = synth.fp_values(E, M, n, 51 + M, 0).astype(np.uint32)
+        b = synth.fp_values(E, M, n, 51 + M, 1).astype(np.uint32)
+        b[: n // 4] = a[: n // 4] ^ (1 << (E + M)) ^ (b[: n // 4] & 7)   # near-cancellation
+        for rnd in (oracle.RN, oracle.RZ):
+            for op in ("add", "mul"):
+                got = oracle.binop(op, E, M, rnd, a, b)
+                for x, y, r in zip(a, b, got):
+                    if any(H.is_nan(E, M, t) or H.is_inf(E, M, t) for t in (x, y)):
+                        continue
+                    vx, vy = H.value(E, M, x), H.value(E, M, y)
+                    v = vx + vy if op == "add" else vx * vy
+                    if v == 0:
+                        continue
+                    _check_rounding(E, M, rnd, v, int(r))
+
+
+# ---------------------------------------------------------------------------
+# invariants
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("E,M", [(3, 2), (4, 4), (5, 7), (6, 9), (8, 23), (3, 23), (8, 2)])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_invariants(E, M, rnd):
+    n = 4096
+    B = 1 + E + M
+    sb = np.uint32(1 << (E + M))
+    x = synth.fp_values(E, M, n, 61, 0).astype(np.uint32)
+    y = synth.fp_values(E, M, n, 61, 1).astype(np.uint32)
+    emask = ((1 << E) - 1) << M
+    fmask = (1 << M) - 1
+    nan = lambda t: ((t & emask) == emask) & ((t & fmask) != 0)
+    fin = lambda t: (t & emask) != emask
+    add = lambda p, q: oracle.binop("add", E, M, rnd, p, q)
+    mul = lambda p, q: oracle.binop("mul", E, M, rnd, p, q)
+    sub = lambda p, q: oracle.binop("sub", E, M, rnd, p, q)
+    assert np.array_equal(add(x, y), add(y, x))
+    assert np.array_equal(mul(x, y), mul(y, x))
+    negz = np.full(n, sb, np.uint32)
+    keep = ~nan(x)
+    assert np.array_equal(add(x, negz)[keep], x[keep])                  # x + (-0) = x
+    one = np.full(n, ((1 << (E - 1)) - 1) << M, np.uint32)
+    assert np.array_equal(mul(x, one)[keep], x[keep])                   # x * 1 = x
+    f = fin(x)
+    assert not sub(x, x)[f].any()                                       # x - x = +0
+    r, rn = add(x, y), add(x ^ sb, y ^ sb)
+    ok = ~nan(r) & ((r & (sb - 1)) != 0)     # an exact-zero sum is +0 both ways
+    assert np.array_equal(rn[ok], (r ^ sb)[ok])                         # sign symmetry
+    m1, m2 = mul(x, y), mul(x ^ sb, y)
+    ok = ~nan(m1)
+    assert np.array_equal(m2[ok], (m1 ^ sb)[ok])
+    assert np.array_equal(sub(x, y), add(x, y ^ sb))
+    assert B <= 32
