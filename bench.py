@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the bitslice custom-precision FP hot path on one GB300.
+
+Workload (one step): element-wise bs_add and bs_mul, round to nearest even,
+on 2^28-element vectors of the 9-bit format 1/4/4 and of the 13-bit format
+1/5/7, operands resident on the device in bitslice form -- four kernel
+launches, 4 * 2^28 elements.  Operands come from the seeded SplitMix64 recipe
+(sign uniform, exponent 98% uniform over the normal range, 1% zero field, 1%
+all-ones field, fraction uniform), drawn on the device and packed once before
+timing.  Every operand (288-416 MB) is larger than the 129 MB L2, so no flush
+is needed between iterations.
+
+Printed: one JSON line with elements/s over the whole job, the roofline of
+the dominant kernel (the slower of its HBM bytes at the measured copy
+bandwidth and of its circuit's gate count at the measured logic-op issue
+rate), the clocks seen during the timed region, an end-to-end figure through
+the C ABI from and to pinned host buffers, and the CPU oracle's throughput on
+a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle itself on the same metric (bounded
+samples of the workload per step); only rank 0 works under torchrun.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "custom-FP elements/s and % roofline for bs_add/bs_mul, batched vs plain; p99 latency"
+UNIT = "elements/s"
+FORMATS = [(4, 4), (5, 7)]
+OPS = ["add", "mul"]
+N = 1 << 28
+RND = 0
+WORKLOAD = ("plain single-format at scale: bs_add + bs_mul (RN) on 1/4/4 and 1/5/7, "
+            "2^28 elements per vector, operands resident in bitslice form")
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from an ncu capture (profiles/), keyed by (E, M, op); None until the
+# kernel as it now stands has been captured.
+NCU_TRAFFIC = {}
+
+
+def apply_tuning() -> int:
+    from paper_1602_04716_gb300 import tune
+    return tune.apply()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def lop3_rate(bs, torch) -> float:
+    """Chip-wide 32-bit logic-op rate (lane-ops/s) from the LOP3 probe."""
+    sms = bs.bsfp_num_sms()
+    grid, block, iters = sms * 8, 256, 4000
+    sink = torch.empty(grid * block, dtype=torch.int32, device="cuda")
+    bs.bsfp_lop3_probe(sink, grid, block, 50)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bs.bsfp_lop3_probe(sink, grid, block, iters)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return grid * block * iters * bs.PROBE_LOP3_PER_ROUND / (best * 1e-3)
+
+
+def cpu_baseline(target_s: float = 12.0):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    per = []
+    m = 1 << 18
+    for E, M in FORMATS:
+        a = synth.fp_values(E, M, m, synth.SEED_A).astype(np.uint32)
+        b = synth.fp_values(E, M, m, synth.SEED_B).astype(np.uint32)
+        for op in OPS:
+            t = time.perf_counter()
+            oracle.binop(op, E, M, RND, a, b)
+            per.append(time.perf_counter() - t)
+    # scale the sample so the timed pass takes about target_s
+    m2 = int(min(1 << 24, max(m, m * target_s / max(sum(per), 1e-6))))
+    tot, els = 0.0, 0
+    for E, M in FORMATS:
+        a = synth.fp_values(E, M, m2, synth.SEED_A).astype(np.uint32)
+        b = synth.fp_values(E, M, m2, synth.SEED_B).astype(np.uint32)
+        for op in OPS:
+            t = time.perf_counter()
+            oracle.binop(op, E, M, RND, a, b)
+            tot += time.perf_counter() - t
+            els += m2
+    return {"value": els / tot, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "first %d elements of each of the 4 (format, op) vectors of the workload "
+                      "(same seeds), %.1f s of oracle time" % (m2, tot)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    m = args.ref_sample
+    data = {}
+    for E, M in FORMATS:
+        data[(E, M)] = (synth.fp_values(E, M, m, synth.SEED_A).astype(np.uint32),
+                        synth.fp_values(E, M, m, synth.SEED_B).astype(np.uint32))
+
+    def step():
+        for E, M in FORMATS:
+            a, b = data[(E, M)]
+            for op in OPS:
+                oracle.binop(op, E, M, RND, a, b)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t) / args.steps
+    value = 4 * m / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_elements_per_vector": m, "formats": ["1/4/4", "1/5/7"],
+                       "ops": OPS, "rounding": "RN"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "first %d elements of each of the 4 (format, op) vectors per step" % m},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1602_04716_gb300 as bs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tuned = apply_tuning()
+    n = args.n
+
+    # ---- operands: drawn on the device, packed once, resident ----
+    bufs = {}
+    for E, M in FORMATS:
+        f = bs.Format(E, M, RND)
+        std = bs.empty_standard(f, n)
+        planes = []
+        for seed in (synth.SEED_A, synth.SEED_B):
+            bs.bsfp_synth_fp_values(f, n, seed, rank, 0, std)
+            p = bs.empty_bitslice(f, n)
+            bs.bsfp_pack(f, std, n, p)
+            planes.append(p)
+        bufs[(E, M)] = (f, planes[0], planes[1], bs.empty_bitslice(f, n))
+        del std
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    kern = [(E, M, op) for E, M in FORMATS for op in OPS]
+
+    def step(evs=None):
+        for i, (E, M, op) in enumerate(kern):
+            f, a, b, out = bufs[(E, M)]
+            if evs is not None:
+                evs[i][0].record(stream)
+            bs.bsfp_op(op, f, a, b, out, n, stream=stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    L = lop3_rate(bs, torch)
+    hbm, hbm_kind = _peaks()
+
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in kern]
+           for _ in range(args.steps)]
+    clocks = Clocks(local) if rank == 0 else None
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = bs.bsfp_launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = bs.bsfp_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    ms_step = ms_max / args.steps
+    value = world * len(kern) * n / (ms_step * 1e-3)
+
+    # ---- per-kernel roofline ----
+    kinfo = []
+    for i, (E, M, op) in enumerate(kern):
+        t = float(np.mean([evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)])) * 1e-3
+        f = bufs[(E, M)][0]
+        B = 1 + E + M
+        G = bs.bsfp_gate_count(f, op)
+        nwords = (n + 31) // 32
+        bytes_ = 3 * B * n / 8
+        r_hbm = hbm * 1e9 / (3 * B / 8)
+        r_alu = L * 32 / G
+        bound = "hbm" if r_hbm <= r_alu else "alu"
+        eps = n / t
+        kinfo.append({"kernel": "bs_%s 1/%d/%d" % (op, E, M), "ms": t * 1e3, "elements_per_s": eps,
+                      "hbm_gbs": bytes_ / t / 1e9, "logic_tops": G * nwords / t / 1e12, "gates_per_word": G,
+                      "wpt": bs.bsfp_variant(f, op), "roofline_elements_per_s": min(r_hbm, r_alu),
+                      "bound": bound, "frac": eps / min(r_hbm, r_alu),
+                      "hbm_frac": bytes_ / t / 1e9 / hbm, "alu_frac": G * nwords / t / L})
+    dom = max(range(len(kern)), key=lambda i: kinfo[i]["ms"])
+    d = kinfo[dom]
+    E, M, op = kern[dom]
+    B = 1 + E + M
+    t = d["ms"] * 1e-3
+    if d["bound"] == "hbm":
+        roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": d["hbm_gbs"] / hbm, "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % hbm_kind}
+    else:
+        roof = {"bound": "alu", "achieved": d["logic_tops"], "peak": L / 1e12, "unit": "Tops/s",
+                "frac": d["logic_tops"] * 1e12 / L,
+                "peak_source": "measured LOP3 issue rate (bsfp_lop3_probe, this run)"}
+    tr = NCU_TRAFFIC.get((E, M, op))
+    roof.update({"kernel": d["kernel"], "traffic": tr,
+                 "algorithmic_bytes": 3 * B * n / 8, "gate_ops": d["gates_per_word"] * ((n + 31) // 32),
+                 "hbm_peak_gbs": hbm, "logic_peak_tops": L / 1e12})
+
+    # ---- end to end through the C ABI from pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(bs, torch, n, rank, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "formats": ["1/4/4", "1/5/7"], "ops": OPS, "rounding": "RN",
+                           "elements_per_vector": n, "launches_per_step": len(kern),
+                           "l2": "no flush: every operand (288-416 MB) exceeds the 129 MB L2",
+                           "seeds": [synth.SEED_A, synth.SEED_B], "parallelism": "dp%d" % world,
+                           "tuned_shapes_applied": tuned},
+                "roofline": roof, "kernels": kinfo, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(bs, torch, n, rank, args):
+    """Per step: pinned host standard arrays -> device -> pack -> add, mul ->
+    unpack -> host, for both formats, all through the library's C ABI."""
+    host_in, dev_std, dev_pl, host_out = {}, {}, {}, {}
+    for E, M in FORMATS:
+        f = bs.Format(E, M, RND)
+        ins = []
+        for seed in (synth.SEED_A, synth.SEED_B):
+            d = bs.empty_standard(f, n)
+            bs.bsfp_synth_fp_values(f, n, seed, rank, 0, d)
+            h = torch.empty(n, dtype=d.dtype, pin_memory=True)
+            h.copy_(d)
+            ins.append(h)
+            del d
+        host_in[(E, M)] = ins
+        dev_std[(E, M)] = [bs.empty_standard(f, n) for _ in range(2)]
+        dev_pl[(E, M)] = [bs.empty_bitslice(f, n) for _ in range(3)]
+        host_out[(E, M)] = [torch.empty(n, dtype=ins[0].dtype, pin_memory=True) for _ in OPS]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        for E, M in FORMATS:
+            f = bs.Format(E, M, RND)
+            (ha, hb), (da, db), (pa, pb, po) = host_in[(E, M)], dev_std[(E, M)], dev_pl[(E, M)]
+            da.copy_(ha, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            h2d += ha.numel() * ha.element_size() * 2
+            bs.bsfp_pack(f, da, n, pa, stream=stream)
+            bs.bsfp_pack(f, db, n, pb, stream=stream)
+            for j, op in enumerate(OPS):
+                bs.bsfp_op(op, f, pa, pb, po, n, stream=stream)
+                bs.bsfp_unpack(f, po, n, da, stream=stream)
+                host_out[(E, M)][j].copy_(da, non_blocking=True)
+                d2h += da.numel() * da.element_size()
+                # da is reused: the next unpack waits for this copy on the same stream
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    k = max(1, args.e2e_steps)
+    t = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t) / k
+    dev_ms = e0.elapsed_time(e1) / k
+    sec = max(wall, dev_ms * 1e-3)
+    return {"value": len(FORMATS) * len(OPS) * n / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k,
+            "path": "pinned host -> H2D -> bsfp_pack -> bsfp_add/bsfp_mul -> bsfp_unpack -> D2H, per format"}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["bsfp", "reference"], default="bsfp")
+    ap.add_argument("--n", type=int, default=N, help="elements per vector (default 2^28)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=1 << 20,
+                    help="reference arm: elements per vector per step")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,144 @@
+/*
+ * bsfp.h -- C ABI of libbsfp: bitslice custom-precision floating point on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * The operations are those of Xu & Gregg, "Customizable Precision of
+ * Floating-Point Arithmetic with Bitslice Vector Types" (arXiv 1602.04716):
+ * vectors of floats of a programmer-chosen format, stored in bitslice form,
+ * with add/sub and mul computed by software logic circuits over whole words
+ * (Sec. 3-4), rounding to nearest-even or toward zero (Sec. 4).
+ *
+ * FORMAT.  1/E/M: one sign bit, E exponent bits (bias 2^(E-1)-1), M fraction
+ * bits, B = 1+E+M <= 32; 2 <= E <= 8, 1 <= M <= 23.  The paper's FP8, FP16
+ * and FP32 (Sec. 5.2) are 1/4/3, 1/5/10 and 1/8/23.  Exponent field 0 encodes
+ * zero and subnormals, the all-ones field Inf (fraction 0) and NaN (otherwise),
+ * as in IEEE 754; results that are NaN are the canonical NaN (sign 0, fraction
+ * 1 << (M-1)).  RN overflows to Inf, RZ to the largest finite value; an exact
+ * zero sum is +0 unless both addends are -0.  Every result is the exact
+ * result rounded once.
+ *
+ * STANDARD REPRESENTATION.  Element i is its B-bit encoding, right-aligned in
+ * a uint8_t (B <= 8), uint16_t (B <= 16) or uint32_t (B <= 32) container at
+ * index i.  Bits above B are ignored on input and zero on output.
+ *
+ * BITSLICE REPRESENTATION (Sec. 2, Fig. 1; Sec. 4, Fig. 3).  B planes of S =
+ * bsfp_plane_stride(n) 32-bit words, plane b at word offset b*S.  Bit b of
+ * element i is bit (i mod 32) of word b*S + i/32: plane 0 is the least
+ * significant fraction bit, planes M..M+E-1 the exponent, plane B-1 the sign.
+ * Lanes past n and words past ceil(n/32) are padding; every output of this
+ * library writes them as zero.
+ *
+ * CONVENTIONS.  All pointers passed to pack/unpack/ops are device memory owned
+ * by the caller; the library never allocates or frees on these calls and
+ * keeps no pointer after it returns.  Bitslice pointers must be 16-byte
+ * aligned; standard arrays aligned to their container size.  Calls are
+ * asynchronous on the given stream (NULL = the legacy default stream); a
+ * validation error returns before anything is launched, a launch error
+ * returns BSFP_ERR_CUDA.  n == 0 is valid and launches nothing.  An output
+ * may be the same pointer as an input; partial overlap is undefined.  Calls
+ * act on the current CUDA device.
+ */
+#ifndef BSFP_H
+#define BSFP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+struct CUstream_st;
+typedef struct CUstream_st* bsfp_stream_t;
+
+/* Rounding (Sec. 4): round to nearest, ties to even; round toward zero. */
+typedef enum { BSFP_RN = 0, BSFP_RZ = 1 } bsfp_round;
+
+/* Format 1/E/M with rounding mode.  Passed by value. */
+typedef struct {
+    int32_t exp_bits; /* E, 2..8 */
+    int32_t man_bits; /* M, 1..23 */
+    int32_t rnd;      /* bsfp_round */
+} bsfp_format;
+
+typedef enum {
+    BSFP_OK = 0,
+    BSFP_ERR_FORMAT = -1,      /* E, M or rounding out of range */
+    BSFP_ERR_NULL = -2,        /* required pointer is NULL */
+    BSFP_ERR_ALIGN = -3,       /* pointer not aligned as required */
+    BSFP_ERR_SIZE = -4,        /* n < 0 or n > BSFP_MAX_N, or a bad count */
+    BSFP_ERR_UNSUPPORTED = -5, /* valid request that this build does not cover */
+    BSFP_ERR_CUDA = -6,        /* a CUDA call failed; see bsfp_last_cuda_error */
+    BSFP_ERR_BUDGET = -7,      /* reserved for admission control */
+    BSFP_ERR_TIMEOUT = -8      /* a bounded wait ran out */
+} bsfp_status;
+
+/* Operation codes (bsfp_op_name, batch jobs, autotune, gate count). */
+typedef enum { BSFP_OP_ADD = 0, BSFP_OP_SUB = 1, BSFP_OP_MUL = 2, BSFP_OP_FMA2 = 3 } bsfp_op;
+
+#define BSFP_MAX_N (((int64_t)1) << 40)
+
+/* ---------------------------------------------------------------- sizes --- */
+/* Plane stride in 32-bit words for n elements: ceil(n/32) rounded up to a
+ * multiple of 32 (128-byte plane rows).  n < 0 returns -1. */
+int64_t bsfp_plane_stride(int64_t n);
+/* Bytes of one bitslice operand: B * stride * 4; -1 on a bad format or n. */
+int64_t bsfp_bitslice_bytes(bsfp_format f, int64_t n);
+/* Container bytes of the standard representation: 1, 2 or 4; -1 on a bad
+ * format. */
+int32_t bsfp_container_bytes(bsfp_format f);
+
+/* ------------------------------------------------------- pack / unpack --- */
+/* pack (Sec. 4, "helper operations for transforming data in the standard
+ * format"; layout Sec. 2, Fig. 1): std_in[n] containers -> bs_out (B planes
+ * of stride bsfp_plane_stride(n)).  Padding of bs_out is written as zero.
+ * std_in must not overlap bs_out. */
+bsfp_status bsfp_pack(bsfp_format f, const void* std_in, int64_t n, uint32_t* bs_out, bsfp_stream_t s);
+/* unpack: the inverse of pack; writes exactly n containers of std_out. */
+bsfp_status bsfp_unpack(bsfp_format f, const uint32_t* bs_in, int64_t n, void* std_out, bsfp_stream_t s);
+
+/* ------------------------------------------------------------------ ops --- */
+/* out = a + b, element-wise, one rounding (Sec. 4, Table 1 row Add/Sub). */
+bsfp_status bsfp_add(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                     bsfp_stream_t s);
+/* out = a - b = a + (-b) (Sec. 4, Table 1 row Add/Sub). */
+bsfp_status bsfp_sub(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                     bsfp_stream_t s);
+/* out = a * b, one rounding (Sec. 4, Table 1 row Mul). */
+bsfp_status bsfp_mul(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                     bsfp_stream_t s);
+/* out = (a * b) + c with two roundings: the product is rounded to the format,
+ * kept in registers, then added and rounded again.  Not in the paper; its
+ * register reuse follows the locality advice of Sec. 4. */
+bsfp_status bsfp_fma2(bsfp_format f, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
+                      int64_t n, bsfp_stream_t s);
+
+/* ---------------------------------------------------------- diagnostics --- */
+const char* bsfp_status_str(int32_t status);
+/* The cudaError_t of the last BSFP_ERR_CUDA on this thread (0 if none). */
+int32_t bsfp_last_cuda_error(void);
+/* Number of 3-input logic gates per 32-element word of the circuit for
+ * (format, op) as built (inversions folded, identical gates shared, dead
+ * gates dropped): the work term of the logic roofline.  Table 1 of Sec. 4
+ * gives only the asymptotic classes.  -1 on a bad argument. */
+int64_t bsfp_gate_count(bsfp_format f, int32_t op);
+/* Words per thread the op kernel will use for (format, op): 1, 2 or 4; -1 on
+ * a bad argument, 0 if the format is not compiled. */
+int32_t bsfp_variant(bsfp_format f, int32_t op);
+/* Bit mask of the words-per-thread variants compiled for (format, op):
+ * bit 0 = 1, bit 1 = 2, bit 2 = 4. */
+int32_t bsfp_variants_compiled(bsfp_format f, int32_t op);
+/* Override the launch shape for (format, op): wpt in {1,2,4} (must be
+ * compiled; 0 restores the default) and blocks_per_sm (0 = occupancy
+ * maximum, larger values are capped at it).  sub shares add's shape.  Used by
+ * the autotuner; returns BSFP_ERR_UNSUPPORTED for an uncompiled wpt.  Not
+ * synchronised with launches already queued: it affects later calls. */
+bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blocks_per_sm);
+/* Kernel launches this library has issued on this process so far. */
+int64_t bsfp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSFP_H */

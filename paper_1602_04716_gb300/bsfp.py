@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libbsfp (include/bsfp.h, include/bsfp_bench.h).
+
+Argument marshalling only: every step of pack, unpack and the arithmetic runs
+in the library's CUDA kernels.  Tensors are passed by ``data_ptr()``; torch
+supplies device memory and the current stream and nothing else.  A non-zero
+status raises ``BsfpError``.  If the library has not been built, every call
+fails loudly: there is no other implementation to fall back on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbsfp.so")
+
+RN, RZ = 0, 1
+OP_ADD, OP_SUB, OP_MUL, OP_FMA2 = 0, 1, 2, 3
+OPS = {"add": OP_ADD, "sub": OP_SUB, "mul": OP_MUL, "fma2": OP_FMA2}
+
+OK = 0
+ERR_FORMAT, ERR_NULL, ERR_ALIGN, ERR_SIZE, ERR_UNSUPPORTED, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT = range(-1, -9, -1)
+PROBE_LOP3_PER_ROUND = 64
+MAX_N = 1 << 40
+
+
+class BsfpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = "%s: %s (%d)" % (where, status_str(status), status)
+        if status == ERR_CUDA:
+            msg += " [cudaError %d]" % _lib().bsfp_last_cuda_error()
+        super().__init__(msg)
+
+
+class bsfp_format(ctypes.Structure):
+    """Format 1/E/M with a rounding mode (RN = 0, RZ = 1)."""
+    _fields_ = [("exp_bits", ctypes.c_int32), ("man_bits", ctypes.c_int32), ("rnd", ctypes.c_int32)]
+
+    def __init__(self, exp_bits: int, man_bits: int, rnd: int = RN):
+        super().__init__(exp_bits, man_bits, rnd)
+
+    @property
+    def bits(self) -> int:
+        return 1 + self.exp_bits + self.man_bits
+
+    def __repr__(self):
+        return "bsfp_format(1/%d/%d, %s)" % (self.exp_bits, self.man_bits, "RZ" if self.rnd else "RN")
+
+
+Format = bsfp_format
+
+_lock = threading.Lock()
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is not None:
+        return _L
+    with _lock:
+        if _L is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libbsfp.so is not built (%s); run __graft_entry__.build() or "
+                                   "python -m paper_1602_04716_gb300.build" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            i32, i64, u32, u64, p = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+            F = bsfp_format
+            sig = {
+                "bsfp_plane_stride": (i64, [i64]),
+                "bsfp_bitslice_bytes": (i64, [F, i64]),
+                "bsfp_container_bytes": (i32, [F]),
+                "bsfp_pack": (i32, [F, p, i64, p, p]),
+                "bsfp_unpack": (i32, [F, p, i64, p, p]),
+                "bsfp_add": (i32, [F, p, p, p, i64, p]),
+                "bsfp_sub": (i32, [F, p, p, p, i64, p]),
+                "bsfp_mul": (i32, [F, p, p, p, i64, p]),
+                "bsfp_fma2": (i32, [F, p, p, p, p, i64, p]),
+                "bsfp_status_str": (ctypes.c_char_p, [i32]),
+                "bsfp_last_cuda_error": (i32, []),
+                "bsfp_gate_count": (i64, [F, i32]),
+                "bsfp_variant": (i32, [F, i32]),
+                "bsfp_variants_compiled": (i32, [F, i32]),
+                "bsfp_set_variant": (i32, [F, i32, i32, i32]),
+                "bsfp_launch_count": (i64, []),
+                "bsfp_synth_fp_values": (i32, [F, i64, u64, u64, i64, p, p]),
+                "bsfp_lop3_probe": (i32, [p, i32, i32, i32, u32, p]),
+                "bsfp_num_sms": (i32, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _L = L
+    return _L
+
+
+def lib_path() -> str:
+    return LIB_PATH
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise BsfpError(status, where)
+
+
+def _fmt(f) -> bsfp_format:
+    if isinstance(f, bsfp_format):
+        return f
+    e, m, *r = f
+    return bsfp_format(e, m, r[0] if r else RN)
+
+
+# ---------------------------------------------------------------- sizes ---
+def bsfp_plane_stride(n: int) -> int:
+    return int(_lib().bsfp_plane_stride(n))
+
+
+def bsfp_bitslice_bytes(f, n: int) -> int:
+    return int(_lib().bsfp_bitslice_bytes(_fmt(f), n))
+
+
+def bsfp_container_bytes(f) -> int:
+    return int(_lib().bsfp_container_bytes(_fmt(f)))
+
+
+# ------------------------------------------------------- pack / unpack ---
+def bsfp_pack(f, std_in, n: int, bs_out, stream=None):
+    _check(_lib().bsfp_pack(_fmt(f), _ptr(std_in), n, _ptr(bs_out), _stream(stream)), "bsfp_pack")
+
+
+def bsfp_unpack(f, bs_in, n: int, std_out, stream=None):
+    _check(_lib().bsfp_unpack(_fmt(f), _ptr(bs_in), n, _ptr(std_out), _stream(stream)), "bsfp_unpack")
+
+
+# ------------------------------------------------------------------ ops ---
+def bsfp_add(f, a, b, out, n: int, stream=None):
+    _check(_lib().bsfp_add(_fmt(f), _ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "bsfp_add")
+
+
+def bsfp_sub(f, a, b, out, n: int, stream=None):
+    _check(_lib().bsfp_sub(_fmt(f), _ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "bsfp_sub")
+
+
+def bsfp_mul(f, a, b, out, n: int, stream=None):
+    _check(_lib().bsfp_mul(_fmt(f), _ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "bsfp_mul")
+
+
+def bsfp_fma2(f, a, b, c, out, n: int, stream=None):
+    _check(_lib().bsfp_fma2(_fmt(f), _ptr(a), _ptr(b), _ptr(c), _ptr(out), n, _stream(stream)), "bsfp_fma2")
+
+
+def bsfp_op(op: str, f, a, b, out, n: int, c=None, stream=None):
+    """Dispatch by name: add, sub, mul or fma2."""
+    if op == "fma2":
+        return bsfp_fma2(f, a, b, c, out, n, stream)
+    return {"add": bsfp_add, "sub": bsfp_sub, "mul": bsfp_mul}[op](f, a, b, out, n, stream)
+
+
+# ---------------------------------------------------------- diagnostics ---
+def status_str(status: int) -> str:
+    return _lib().bsfp_status_str(status).decode()
+
+
+bsfp_status_str = status_str
+
+
+def bsfp_last_cuda_error() -> int:
+    return int(_lib().bsfp_last_cuda_error())
+
+
+def bsfp_gate_count(f, op) -> int:
+    return int(_lib().bsfp_gate_count(_fmt(f), OPS.get(op, op)))
+
+
+def bsfp_variant(f, op) -> int:
+    return int(_lib().bsfp_variant(_fmt(f), OPS.get(op, op)))
+
+
+def bsfp_variants_compiled(f, op) -> list:
+    m = int(_lib().bsfp_variants_compiled(_fmt(f), OPS.get(op, op)))
+    return [w for i, w in enumerate((1, 2, 4)) if m > 0 and (m >> i) & 1]
+
+
+def bsfp_set_variant(f, op, wpt: int, blocks_per_sm: int = 0):
+    _check(_lib().bsfp_set_variant(_fmt(f), OPS.get(op, op), wpt, blocks_per_sm), "bsfp_set_variant")
+
+
+def bsfp_launch_count() -> int:
+    return int(_lib().bsfp_launch_count())
+
+
+# ------------------------------------------------------- bench support ---
+def bsfp_synth_fp_values(f, n: int, seed: int, stream_id: int, start: int, out, stream=None):
+    _check(_lib().bsfp_synth_fp_values(_fmt(f), n, seed, stream_id, start, _ptr(out), _stream(stream)),
+           "bsfp_synth_fp_values")
+
+
+def bsfp_lop3_probe(sink, grid: int, block: int, iters: int, seed: int = 1, stream=None):
+    _check(_lib().bsfp_lop3_probe(_ptr(sink), grid, block, iters, seed, _stream(stream)), "bsfp_lop3_probe")
+
+
+def bsfp_num_sms() -> int:
+    return int(_lib().bsfp_num_sms())
+
+
+# ------------------------------------------------- torch conveniences ---
+def container_dtype(f):
+    """torch dtype of the standard representation (same bytes as uint8/16/32)."""
+    import torch
+    cb = bsfp_container_bytes(f)
+    return {1: torch.uint8, 2: torch.int16, 4: torch.int32}[cb]
+
+
+def empty_bitslice(f, n: int, device="cuda"):
+    """An uninitialised bitslice operand: B*S int32 words (viewed as uint32)."""
+    import torch
+    f = _fmt(f)
+    return torch.empty(f.bits * bsfp_plane_stride(n), dtype=torch.int32, device=device)
+
+
+def empty_standard(f, n: int, device="cuda"):
+    import torch
+    return torch.empty(n, dtype=container_dtype(f), device=device)

@@ -1,0 +1,96 @@
+"""Builds libbsfp.so (the CUDA library) in-tree for sm_103a.
+
+Every translation unit compiles in parallel with one ``-gencode`` (sm_103a);
+the element-wise kernels are split by exponent width and fraction range so
+the instantiations spread over the cores.  Objects go to ``_build/`` next to
+this file and are rebuilt only when a source or header is newer.
+"""
+from __future__ import annotations
+
+import glob
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INC = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libbsfp.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found")
+
+
+def _units():
+    """(object name, compiler command without -o) for every translation unit."""
+    nv = nvcc()
+    cu = [nv, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INC, "-c"]
+    units = []
+    for e in range(2, 9):
+        for lo, hi in ((1, 11), (12, 23)):
+            units.append(("binop_e%d_m%d.o" % (e, lo),
+                          cu + ["-DBSFP_E=%d" % e, "-DBSFP_M_LO=%d" % lo, "-DBSFP_M_HI=%d" % hi,
+                                os.path.join(CSRC, "binop_inst.cu")]))
+        units.append(("gatecount_e%d.o" % e,
+                      ["g++", "-std=c++17", "-O1", "-fPIC", "-I", CSRC, "-DBSFP_E=%d" % e, "-c",
+                       os.path.join(CSRC, "gatecount.cpp")]))
+    for src in ("api.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):
+        units.append((src.replace(".cu", ".o"), cu + [os.path.join(CSRC, src)]))
+    return units
+
+
+def _deps():
+    return glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INC, "*.h"))
+
+
+def build(jobs: int | None = None, verbose: bool = False) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _deps())
+    units = _units()
+    todo = [(o, c) for o, c in units
+            if not os.path.exists(os.path.join(BUILD, o)) or os.path.getmtime(os.path.join(BUILD, o)) < newest]
+    jobs = jobs or max(1, os.cpu_count() or 1)
+
+    def run(item):
+        o, cmd = item
+        out = os.path.join(BUILD, o)
+        tmp = out + ".tmp"
+        r = subprocess.run(cmd + ["-o", tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            return o, r.stdout + r.stderr
+        os.replace(tmp, out)
+        return o, None
+
+    # longest units first
+    todo.sort(key=lambda t: (not t[0].startswith("binop"), t[0]))
+    errors = []
+    with ThreadPoolExecutor(jobs) as ex:
+        for o, err in ex.map(run, todo):
+            if err:
+                errors.append("%s:\n%s" % (o, err))
+            elif verbose:
+                print("built", o, file=sys.stderr)
+    if errors:
+        raise RuntimeError("libbsfp build failed:\n" + "\n".join(errors))
+    objs = [os.path.join(BUILD, o) for o, _ in units]
+    if todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(p) for p in objs):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+                               "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(verbose=True)
+    print(LIB)

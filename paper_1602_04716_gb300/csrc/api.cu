@@ -1,0 +1,279 @@
+/*
+ * api.cu -- the C ABI of libbsfp (declared in include/bsfp.h): argument
+ * validation, the (format, op) dispatch table, launch shapes and the
+ * autotuner's overrides.
+ *
+ * The paper's library generator (Sec. 5.1) turned a configuration file of
+ * exponent bits, mantissa bits and rounding mode into a header plus a shared
+ * library specialised to that format.  Here every format 1/E/M with
+ * 2 <= E <= 8, 1 <= M <= 23 is compiled ahead of time as C++ template
+ * instances, and the format becomes a run-time argument that selects the
+ * instance from a table.
+ */
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "binop.cuh"
+#include "bsfp.h"
+
+namespace bsfp {
+
+BinopEntry g_binop_table[TAB_E][TAB_M][2][OPC_COUNT];
+
+/* Each exponent width is compiled as two translation units, M in [1, 11]
+ * and [12, 23]; each fills its part of the table. */
+#define BSFP_DECL_REG(E) void register_e##E##_m1(); void register_e##E##_m12();
+BSFP_DECL_REG(2) BSFP_DECL_REG(3) BSFP_DECL_REG(4) BSFP_DECL_REG(5) BSFP_DECL_REG(6) BSFP_DECL_REG(7)
+BSFP_DECL_REG(8)
+#undef BSFP_DECL_REG
+
+cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st);
+cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st);
+int device_num_sms();
+
+static std::once_flag g_init_once;
+static void init_tables() {
+    register_e2_m1(); register_e2_m12();
+    register_e3_m1(); register_e3_m12();
+    register_e4_m1(); register_e4_m12();
+    register_e5_m1(); register_e5_m12();
+    register_e6_m1(); register_e6_m12();
+    register_e7_m1(); register_e7_m12();
+    register_e8_m1(); register_e8_m12();
+}
+
+/* Launch shape per (E, M, rounding, op class): words per thread and resident
+ * blocks per SM (0 = the occupancy maximum). */
+struct Shape {
+    int8_t wpt;
+    int16_t bps;
+};
+static Shape g_shape[TAB_E][TAB_M][2][OPC_COUNT];
+static int g_occ[TAB_E][TAB_M][2][OPC_COUNT][5];   /* cached occupancy per wpt */
+static std::mutex g_shape_mu;
+
+static std::atomic<int64_t> g_launches{0};
+static thread_local int32_t g_last_cuda = 0;
+
+static bsfp_status cuda_fail(cudaError_t e) {
+    g_last_cuda = (int32_t)e;
+    return BSFP_ERR_CUDA;
+}
+
+static bool format_ok(const bsfp_format& f) {
+    return f.exp_bits >= 2 && f.exp_bits <= 8 && f.man_bits >= 1 && f.man_bits <= 23 &&
+           1 + f.exp_bits + f.man_bits <= 32 && (f.rnd == BSFP_RN || f.rnd == BSFP_RZ);
+}
+
+static int bits_of(const bsfp_format& f) { return 1 + f.exp_bits + f.man_bits; }
+
+static bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+static int opclass(int op) {
+    switch (op) {
+        case BSFP_OP_ADD:
+        case BSFP_OP_SUB: return OPC_ADDSUB;
+        case BSFP_OP_MUL: return OPC_MUL;
+        case BSFP_OP_FMA2: return OPC_FMA2;
+    }
+    return -1;
+}
+
+static const BinopEntry* entry_for(const bsfp_format& f, int opc) {
+    std::call_once(g_init_once, init_tables);
+    const BinopEntry* e = &g_binop_table[f.exp_bits][f.man_bits][f.rnd][opc];
+    return e->launch ? e : nullptr;
+}
+
+static int occupancy(const bsfp_format& f, int opc, const BinopEntry* e, int wpt) {
+    int& o = g_occ[f.exp_bits][f.man_bits][f.rnd][opc][wpt];
+    if (o == 0) {
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->kernel(wpt), 128, 0) != cudaSuccess || blocks < 1)
+            blocks = 1;
+        o = blocks;
+    }
+    return o;
+}
+
+/* Run one element-wise op. */
+static bsfp_status run_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                             uint32_t* out, int64_t n, cudaStream_t s) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    const int opc = opclass(op);
+    if (!a || !b || !out || (opc == OPC_FMA2 && !c)) return BSFP_ERR_NULL;
+    if (!aligned(a, 16) || !aligned(b, 16) || !aligned(out, 16) || (opc == OPC_FMA2 && !aligned(c, 16)))
+        return BSFP_ERR_ALIGN;
+    const BinopEntry* e = entry_for(f, opc);
+    if (!e) return BSFP_ERR_UNSUPPORTED;
+
+    BinopArgs p;
+    p.a = a;
+    p.b = b;
+    p.c = c;
+    p.out = out;
+    p.S = bsfp_plane_stride(n);
+    p.nwords = (n + 31) / 32;
+    p.tailmask = (n % 32) ? ((1u << (n % 32)) - 1u) : ~0u;
+    p.negb = (op == BSFP_OP_SUB) ? ~0u : 0u;
+
+    int wpt, bps;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+        wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
+        const int occ = occupancy(f, opc, e, wpt);
+        bps = (sh.bps > 0 && sh.bps < occ) ? sh.bps : occ;
+    }
+    const int64_t chunks = p.S / wpt;
+    const int64_t need = (chunks + 127) / 128;
+    const int64_t cap = (int64_t)device_num_sms() * bps;
+    const int grid = (int)(need < cap ? need : cap);
+    const cudaError_t err = e->launch(p, wpt, grid, s);
+    if (err != cudaSuccess) return cuda_fail(err);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+}  // namespace bsfp
+
+using namespace bsfp;
+
+extern "C" {
+
+int64_t bsfp_plane_stride(int64_t n) {
+    if (n < 0) return -1;
+    const int64_t words = (n + 31) / 32;
+    return (words + 31) / 32 * 32;
+}
+
+int64_t bsfp_bitslice_bytes(bsfp_format f, int64_t n) {
+    if (!format_ok(f) || n < 0 || n > BSFP_MAX_N) return -1;
+    return (int64_t)bits_of(f) * bsfp_plane_stride(n) * 4;
+}
+
+int32_t bsfp_container_bytes(bsfp_format f) {
+    if (!format_ok(f)) return -1;
+    const int B = bits_of(f);
+    return B <= 8 ? 1 : (B <= 16 ? 2 : 4);
+}
+
+bsfp_status bsfp_pack(bsfp_format f, const void* std_in, int64_t n, uint32_t* bs_out, bsfp_stream_t s) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    if (!std_in || !bs_out) return BSFP_ERR_NULL;
+    const int cb = bsfp_container_bytes(f);
+    if (!aligned(std_in, (uintptr_t)cb) || !aligned(bs_out, 16)) return BSFP_ERR_ALIGN;
+    const cudaError_t e = launch_pack(cb, std_in, n, bits_of(f), bs_out, bsfp_plane_stride(n), (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+bsfp_status bsfp_unpack(bsfp_format f, const uint32_t* bs_in, int64_t n, void* std_out, bsfp_stream_t s) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    if (!bs_in || !std_out) return BSFP_ERR_NULL;
+    const int cb = bsfp_container_bytes(f);
+    if (!aligned(bs_in, 16) || !aligned(std_out, (uintptr_t)cb)) return BSFP_ERR_ALIGN;
+    const cudaError_t e = launch_unpack(cb, bs_in, bsfp_plane_stride(n), bits_of(f), std_out, n, (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+bsfp_status bsfp_add(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n, bsfp_stream_t s) {
+    return run_binop(f, BSFP_OP_ADD, a, b, nullptr, out, n, (cudaStream_t)s);
+}
+
+bsfp_status bsfp_sub(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n, bsfp_stream_t s) {
+    return run_binop(f, BSFP_OP_SUB, a, b, nullptr, out, n, (cudaStream_t)s);
+}
+
+bsfp_status bsfp_mul(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n, bsfp_stream_t s) {
+    return run_binop(f, BSFP_OP_MUL, a, b, nullptr, out, n, (cudaStream_t)s);
+}
+
+bsfp_status bsfp_fma2(bsfp_format f, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
+                      int64_t n, bsfp_stream_t s) {
+    return run_binop(f, BSFP_OP_FMA2, a, b, c, out, n, (cudaStream_t)s);
+}
+
+const char* bsfp_status_str(int32_t status) {
+    switch (status) {
+        case BSFP_OK: return "ok";
+        case BSFP_ERR_FORMAT: return "format out of range (need 2<=E<=8, 1<=M<=23, rounding RN or RZ)";
+        case BSFP_ERR_NULL: return "null pointer";
+        case BSFP_ERR_ALIGN: return "misaligned pointer (bitslice: 16 bytes; standard: container size)";
+        case BSFP_ERR_SIZE: return "size out of range";
+        case BSFP_ERR_UNSUPPORTED: return "not compiled into this build";
+        case BSFP_ERR_CUDA: return "CUDA error";
+        case BSFP_ERR_BUDGET: return "over the memory budget";
+        case BSFP_ERR_TIMEOUT: return "timed out";
+    }
+    return "unknown status";
+}
+
+int32_t bsfp_last_cuda_error(void) { return g_last_cuda; }
+
+long bsfp_gate_count_e2(int, int, int);
+long bsfp_gate_count_e3(int, int, int);
+long bsfp_gate_count_e4(int, int, int);
+long bsfp_gate_count_e5(int, int, int);
+long bsfp_gate_count_e6(int, int, int);
+long bsfp_gate_count_e7(int, int, int);
+long bsfp_gate_count_e8(int, int, int);
+
+int64_t bsfp_gate_count(bsfp_format f, int32_t op) {
+    if (!format_ok(f) || op < 0 || op > 3) return -1;
+    const int m = f.man_bits, r = f.rnd;
+    switch (f.exp_bits) {
+        case 2: return bsfp_gate_count_e2(m, r, op);
+        case 3: return bsfp_gate_count_e3(m, r, op);
+        case 4: return bsfp_gate_count_e4(m, r, op);
+        case 5: return bsfp_gate_count_e5(m, r, op);
+        case 6: return bsfp_gate_count_e6(m, r, op);
+        case 7: return bsfp_gate_count_e7(m, r, op);
+        case 8: return bsfp_gate_count_e8(m, r, op);
+    }
+    return -1;
+}
+
+int32_t bsfp_variants_compiled(bsfp_format f, int32_t op) {
+    if (!format_ok(f) || opclass(op) < 0) return -1;
+    const BinopEntry* e = entry_for(f, opclass(op));
+    return e ? (int32_t)e->wpt_mask : 0;
+}
+
+int32_t bsfp_variant(bsfp_format f, int32_t op) {
+    if (!format_ok(f) || opclass(op) < 0) return -1;
+    const int opc = opclass(op);
+    const BinopEntry* e = entry_for(f, opc);
+    if (!e) return 0;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+    return (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
+}
+
+bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blocks_per_sm) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    const int opc = opclass(op);
+    if (opc < 0 || blocks_per_sm < 0 || blocks_per_sm > 64) return BSFP_ERR_SIZE;
+    if (wpt != 0 && wpt != 1 && wpt != 2 && wpt != 4) return BSFP_ERR_SIZE;
+    const BinopEntry* e = entry_for(f, opc);
+    if (!e || (wpt != 0 && !(e->wpt_mask & (unsigned)wpt))) return BSFP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = Shape{(int8_t)wpt, (int16_t)blocks_per_sm};
+    return BSFP_OK;
+}
+
+int64_t bsfp_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

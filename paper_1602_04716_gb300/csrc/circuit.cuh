@@ -1,0 +1,498 @@
+/*
+ * circuit.cuh -- bitslice floating-point circuits (host + device templates).
+ *
+ * Xu & Gregg, "Customizable Precision of Floating-Point Arithmetic with
+ * Bitslice Vector Types" (arXiv 1602.04716).
+ *
+ * A value of the format 1/E/M (one sign bit, E exponent bits with bias
+ * 2^(E-1)-1, M fraction bits) is held as B = 1+E+M words, one word per bit
+ * ("slice"): bit j of slice b is bit b of element j (Sec. 2, Fig. 1).  Slice 0
+ * is the least significant fraction bit, slices M..M+E-1 the exponent,
+ * slice B-1 the sign.  Every operation below is a straight-line logic circuit
+ * over whole words, so one evaluation computes 32 elements at once (Sec. 3,
+ * Fig. 2).
+ *
+ * The operations follow the step structure of Sec. 4, Table 1:
+ *   add/sub : sign, alignment shift (log shifter, Sec. 4), significand add,
+ *             normalisation (log shifter), rounding;
+ *   mul     : sign, exponent add (the two exponent additions merged, Sec. 4),
+ *             significand multiply (carry-save array kept in registers),
+ *             normalisation, rounding.
+ * Rounding is round-to-nearest-even (RN) or round-toward-zero (RZ), both
+ * correctly rounded (Sec. 4).  Where the paper is silent the circuits take the
+ * IEEE-754 reading: gradual underflow, Inf/NaN at the all-ones exponent,
+ * canonical NaN = +, exponent all ones, fraction 1 << (M-1); RN overflow to
+ * Inf and RZ overflow to the largest finite value; an exact-zero sum is +0
+ * unless both addends are -0.
+ *
+ * Gate primitives.  The circuits use only the functions of <= 3 words below;
+ * each compiles to a single LOP3 on sm_103a (a NOT is folded into the LOP3 that
+ * consumes it).  Instantiated with another word type (see gatecount.cpp) the
+ * same templates are counted gate by gate instead of evaluated.  The aim is the
+ * one the paper states for its own circuits (Sec. 4): the fewest gates, not the
+ * shortest latency -- 32 lanes x many warps supply the parallelism.
+ */
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define BSFP_HD __host__ __device__ __forceinline__
+#define BSFP_UNROLL _Pragma("unroll")
+#else
+#define BSFP_HD inline
+#define BSFP_UNROLL _Pragma("GCC unroll 128")
+#endif
+
+namespace bsfp {
+
+/* ---------------------------------------------------------------- gates --- */
+template <class W> BSFP_HD W NOT(W a) { return ~a; }
+template <class W> BSFP_HD W AND(W a, W b) { return a & b; }
+template <class W> BSFP_HD W OR(W a, W b) { return a | b; }
+template <class W> BSFP_HD W XOR(W a, W b) { return a ^ b; }
+template <class W> BSFP_HD W ANDN(W a, W b) { return a & ~b; }            /* a & !b        */
+template <class W> BSFP_HD W XOR3(W a, W b, W c) { return a ^ b ^ c; }
+template <class W> BSFP_HD W MAJ(W a, W b, W c) { return (a & b) | (c & (a | b)); }
+template <class W> BSFP_HD W MUX(W s, W t, W f) { return (s & t) | (~s & f); } /* s ? t : f  */
+template <class W> BSFP_HD W OR3(W a, W b, W c) { return a | b | c; }
+template <class W> BSFP_HD W AND3(W a, W b, W c) { return a & b & c; }
+template <class W> BSFP_HD W ANDOR(W a, W b, W c) { return (a & b) | c; }  /* a&b | c       */
+template <class W> BSFP_HD W ANDNN(W a, W b, W c) { return a & ~b & ~c; }  /* a & !b & !c   */
+/* Any function of three words, given by its truth table L: bit (4a+2b+c) of L
+ * is the output for input bits a, b, c (the LOP3 immediate convention). */
+template <unsigned L, class W> BSFP_HD W F3(W a, W b, W c) {
+    W r = W(0u);
+    if (L & 0x01u) r = r | (~a & ~b & ~c);
+    if (L & 0x02u) r = r | (~a & ~b & c);
+    if (L & 0x04u) r = r | (~a & b & ~c);
+    if (L & 0x08u) r = r | (~a & b & c);
+    if (L & 0x10u) r = r | (a & ~b & ~c);
+    if (L & 0x20u) r = r | (a & ~b & c);
+    if (L & 0x40u) r = r | (a & b & ~c);
+    if (L & 0x80u) r = r | (a & b & c);
+    return r;
+}
+/* Named truth tables used below. */
+constexpr unsigned LUT_G_AND_LS = 0xE0u;     /* g & (l | s)          */
+constexpr unsigned LUT_NZ_BUDGET = 0x0Bu;    /* !top & (!br | hiu)   */
+constexpr unsigned LUT_OR_ANDN = 0x54u;      /* (m | o) & !s         */
+constexpr unsigned LUT_ANDNN = 0x10u;        /* a & !b & !c          */
+constexpr unsigned LUT_MASK_OR = 0xBAu;      /* (m & !z) | f         */
+constexpr unsigned LUT_AND_OR_NOT = 0xD0u;   /* a & (b | !c)         */
+
+/* -------------------------------------------------------- word vectors --- */
+/* OR / AND of n words (n compile-time after inlining). */
+template <int N, class W> BSFP_HD W or_n(const W* x) {
+    if constexpr (N <= 0) {
+        return W(0u);
+    } else {
+        W r = x[0];
+        BSFP_UNROLL
+        for (int i = 1; i < N; i += 2) r = (i + 1 < N) ? OR3(r, x[i], x[i + 1]) : OR(r, x[i]);
+        return r;
+    }
+}
+template <int N, class W> BSFP_HD W and_n(const W* x) {
+    if constexpr (N <= 0) {
+        return ~W(0u);
+    } else {
+        W r = x[0];
+        BSFP_UNROLL
+        for (int i = 1; i < N; i += 2) r = (i + 1 < N) ? AND3(r, x[i], x[i + 1]) : AND(r, x[i]);
+        return r;
+    }
+}
+
+/* One stage of a right log shifter: if dk, x >>= S, with every bit that falls
+ * to position 0 or below ORed into x[0] (the sticky position). */
+template <int N, int S, class W> BSFP_HD void rs_stage(W* x, W dk) {
+    const W st = or_n<S>(x + 1);
+    const W x0 = ANDOR(dk, st, x[0]);
+    BSFP_UNROLL
+    for (int p = 1; p < N; ++p) x[p] = MUX(dk, (p + S < N) ? x[(p + S < N) ? p + S : 0] : W(0u), x[p]);
+    x[0] = x0;
+}
+
+/* x (N words, x[0] = sticky position) >>= d, d unsigned with ND bits (the log
+ * shifter of Sec. 4).  Shift amounts >= N move every bit into the sticky. */
+template <int N, int ND, int K = 0, class W> BSFP_HD void rshift_sticky(W* x, const W* d) {
+    if constexpr (K < ND) {
+        if constexpr ((1 << K) < N) {
+            rs_stage<N, (1 << K)>(x, d[K]);
+            rshift_sticky<N, ND, K + 1>(x, d);
+        } else {
+            const W far = or_n<ND - K>(d + K);
+            const W st = or_n<N - 1>(x + 1);
+            x[0] = ANDOR(far, st, x[0]);
+            BSFP_UNROLL
+            for (int p = 1; p < N; ++p) x[p] = ANDN(x[p], far);
+        }
+    }
+}
+
+constexpr int floor_log2(int v) { return v <= 1 ? 0 : 1 + floor_log2(v / 2); }
+
+/* One stage of the normalising left shifter: shift by S = 2^K when the top S
+ * bits of z are zero and the remaining budget allows it.  The budget test is
+ * u >= (t[KT..K+1], 1, 0..0), i.e. u - (shift already taken) >= S, done as a
+ * borrow chain over bits K..KT of u; hiu = some bit of u above KT is set. */
+template <int N, int NU, int KT, int K, class W>
+BSFP_HD void ln_stage(W* z, const W* u, W hiu, W* t) {
+    constexpr int S = 1 << K;
+    W c;
+    if constexpr (K >= NU) {
+        c = W(0u);                       /* budget < 2^NU <= S: never shift */
+    } else {
+        const W top = or_n<S>(z + N - S);
+        W br = NOT(u[K]);
+        BSFP_UNROLL
+        for (int j = K + 1; j <= KT && j < NU; ++j) br = MAJ(NOT(u[j]), t[j], br);
+        c = F3<LUT_NZ_BUDGET>(top, br, hiu);
+    }
+    t[K] = c;
+    BSFP_UNROLL
+    for (int p = N - 1; p >= 0; --p) z[p] = MUX(c, (p >= S) ? z[(p >= S) ? p - S : 0] : W(0u), z[p]);
+}
+
+template <int N, int NU, int KT, int K, class W>
+BSFP_HD void ln_stages(W* z, const W* u, W hiu, W* t) {
+    ln_stage<N, NU, KT, K>(z, u, hiu, t);
+    if constexpr (K > 0) ln_stages<N, NU, KT, K - 1>(z, u, hiu, t);
+}
+
+/* Normalise z (N words, z[N-1] = top) left by t = min(lz(z), u) where u is an
+ * unsigned NU-bit budget; writes the shift t[0..KT], KT = floor(log2(N-1)).
+ * Greedy from the largest stage down: each stage removes 2^K leading zeros
+ * when both the zeros and the budget allow, which decomposes min(lz, u)
+ * exactly (the normalisation log shifter of Sec. 4, Table 1). */
+template <int N, int NU, class W> BSFP_HD void lnorm(W* z, const W* u, W* t) {
+    constexpr int KT = floor_log2(N - 1);
+    W hiu = W(0u);
+    if constexpr (KT + 1 < NU) hiu = or_n<NU - KT - 1>(u + KT + 1);
+    ln_stages<N, NU, KT, KT>(z, u, hiu, t);
+}
+
+/* D = u - t (u: NU bits, t: NT bits, u >= t), NU-bit result. */
+template <int NU, int NT, class W> BSFP_HD void sub_un(const W* u, const W* t, W* D) {
+    W br = W(0u);
+    BSFP_UNROLL
+    for (int i = 0; i < NU; ++i) {
+        const W ti = (i < NT) ? t[(i < NT) ? i : 0] : W(0u);
+        D[i] = XOR3(u[i], ti, br);
+        if (i + 1 < NU) br = MAJ(NOT(u[i]), ti, br);
+    }
+}
+
+/* mag = (D << M) + sig + rup, sig has M+1 bits (sig[M] = leading bit), D has
+ * ND bits; mag has M+ND+1 bits.  Adding the leading bit into the exponent
+ * field and the rounding carry through the whole magnitude is the usual
+ * encoding trick: a fraction that rounds up from all ones increments the
+ * exponent, and a subnormal that rounds up to 2^M becomes the least normal. */
+template <int M, int ND, class W> BSFP_HD void assemble(const W* D, const W* sig, W rup, W* mag) {
+    W c = rup;
+    BSFP_UNROLL
+    for (int i = 0; i < M; ++i) {
+        mag[i] = XOR(sig[i], c);
+        c = AND(sig[i], c);
+    }
+    mag[M] = XOR3(sig[M], D[0], c);
+    c = MAJ(sig[M], D[0], c);
+    BSFP_UNROLL
+    for (int i = 1; i < ND; ++i) {
+        mag[M + i] = XOR(D[i], c);
+        c = AND(D[i], c);
+    }
+    mag[M + ND] = c;
+}
+
+/* Final encoding.  mag: M+NF bits (NF >= E field bits, higher ones only ever
+ * signal overflow); spec: the result is Inf or NaN; nan: it is NaN; zero: the
+ * exact result is zero (its exponent bits in mag are then meaningless, since
+ * the normaliser cannot always shift a zero significand all the way down);
+ * sgn: sign of the result unless zs (an exact zero that is +0).  RN overflows
+ * to Inf, RZ to max finite. */
+template <int E, int M, int NF, bool RZ, class W>
+BSFP_HD void encode(const W* mag, W spec, W nan, W zero, W sgn, W zs, W* r) {
+    constexpr int B = 1 + E + M;
+    W ovf = and_n<E>(mag + M);
+    if constexpr (NF > E) ovf = OR(ovf, or_n<NF - E>(mag + M + E));
+    if constexpr (!RZ) {
+        const W force = OR(ANDN(ovf, zero), spec);
+        BSFP_UNROLL
+        for (int i = 0; i < E; ++i) r[M + i] = F3<LUT_MASK_OR>(mag[M + i], zero, force);
+        BSFP_UNROLL
+        for (int i = 0; i + 1 < M; ++i) r[i] = ANDN(mag[i], force);
+        r[M - 1] = MUX(force, nan, mag[M - 1]);
+    } else {
+        /* overflow -> exponent 2^E-2, fraction all ones; Inf/NaN -> all-ones
+         * exponent with fraction 0 / 1 << (M-1) */
+        const W ov = ANDN(ovf, zero);
+        const W ovs = OR(ov, spec);
+        r[M] = ANDOR(mag[M], NOT(OR(ovf, zero)), spec);
+        BSFP_UNROLL
+        for (int i = 1; i < E; ++i) r[M + i] = F3<LUT_MASK_OR>(mag[M + i], zero, ovs);
+        BSFP_UNROLL
+        for (int i = 0; i + 1 < M; ++i) r[i] = F3<LUT_OR_ANDN>(mag[i], ov, spec);
+        r[M - 1] = MUX(spec, nan, OR(mag[M - 1], ov));
+    }
+    r[B - 1] = F3<LUT_ANDNN>(sgn, zs, nan);
+}
+
+/* -------------------------------------------------------------- add/sub --- */
+/* r = a + b (NEG_B: a - b), one rounding (Sec. 4, Table 1, Add/Sub). */
+template <int E, int M, bool RZ, bool NEG_B, class W>
+BSFP_HD void fp_add(const W* a, const W* b, W* r) {
+    static_assert(E >= 2 && M >= 1 && 1 + E + M <= 32, "format out of range");
+    constexpr int B = 1 + E + M;
+    constexpr int NM = E + M;   /* magnitude bits */
+    const W sa = a[B - 1];
+    const W sb = NEG_B ? NOT(b[B - 1]) : b[B - 1];
+
+    /* step 1 (sign): order the operands by magnitude, |X| >= |Y| -- a borrow
+     * chain of |a| - |b| */
+    W br = ANDN(b[0], a[0]);
+    BSFP_UNROLL
+    for (int i = 1; i < NM; ++i) br = MAJ(NOT(a[i]), b[i], br);
+    const W sw = br;   /* |a| < |b| */
+    W X[NM], Y[NM];
+    BSFP_UNROLL
+    for (int i = 0; i < NM; ++i) {
+        X[i] = MUX(sw, b[i], a[i]);
+        Y[i] = MUX(sw, a[i], b[i]);
+    }
+    const W sX = MUX(sw, sb, sa);
+    const W esub = XOR(sa, sb);         /* effective subtraction */
+    const W* eX = X + M;
+    const W* eY = Y + M;
+    const W nzX = or_n<E>(eX);          /* implicit bits: exponent field != 0 */
+    const W nzY = or_n<E>(eY);
+
+    /* exponent difference d = max(eX,1) - max(eY,1) >= 0 */
+    W d[E];
+    br = ANDN(nzX, nzY);
+    BSFP_UNROLL
+    for (int i = 0; i < E; ++i) {
+        d[i] = XOR3(eX[i], eY[i], br);
+        if (i + 1 < E) br = MAJ(NOT(eX[i]), eY[i], br);
+    }
+
+    /* step 2 (alignment shift): y = 1.fY (or 0.fY) at positions 3..M+3 above
+     * guard (2), round (1) and sticky (0) */
+    constexpr int NY = M + 4;
+    W y[NY];
+    y[0] = y[1] = y[2] = W(0u);
+    BSFP_UNROLL
+    for (int i = 0; i < M; ++i) y[3 + i] = Y[i];
+    y[M + 3] = nzY;
+    rshift_sticky<NY, E>(y, d);
+
+    /* step 3 (add): z = x +/- y over M+5 positions (M+4 = carry out) */
+    constexpr int NZ = M + 5;
+    W z[NZ];
+    W c = esub;
+    BSFP_UNROLL
+    for (int p = 0; p < NY; ++p) {
+        const W xp = (p < 3) ? W(0u) : (p < M + 3 ? X[(p >= 3 && p < M + 3) ? p - 3 : 0] : nzX);
+        const W yp = XOR(y[p], esub);
+        z[p] = XOR3(xp, yp, c);
+        c = MAJ(xp, yp, c);
+    }
+    z[NZ - 1] = ANDN(c, esub);
+
+    /* step 4 (normalisation): shift left by t = min(lz(z), max(eX,1)); the
+     * result exponent field is max(eX,1) + 1 - t, and a result that cannot be
+     * normalised within that budget is subnormal */
+    W u[E];
+    u[0] = OR(eX[0], NOT(nzX));
+    BSFP_UNROLL
+    for (int i = 1; i < E; ++i) u[i] = eX[i];
+    constexpr int KT = floor_log2(NZ - 1);
+    W t[KT + 1];
+    lnorm<NZ, E>(z, u, t);
+    W D[E];
+    sub_un<E, KT + 1>(u, t, D);
+
+    /* step 5 (rounding): significand z[M+4..4], guard z[3], sticky z[2..0] */
+    const W* sig = z + 4;
+    W rup = W(0u);
+    if constexpr (!RZ) rup = F3<LUT_G_AND_LS>(z[3], sig[0], OR3(z[2], z[1], z[0]));
+    W mag[M + E + 1];
+    assemble<M, E>(D, sig, rup, mag);
+
+    /* specials: X is NaN or Inf whenever either operand is (|NaN| > |Inf|) */
+    const W xspec = and_n<E>(eX);
+    const W yspec = and_n<E>(eY);
+    const W nan = AND(xspec, ANDOR(yspec, esub, or_n<M>(X)));
+    const W zero = NOT(or_n<M + 1>(sig));            /* exact zero sum */
+    const W zs = AND3(zero, esub, NOT(xspec));       /* x + (-x) = +0 */
+    encode<E, M, E + 1, RZ>(mag, xspec, nan, zero, sX, zs, r);
+}
+
+/* ------------------------------------------------------------------ mul --- */
+/* P = A * B for n-bit unsigned A, B: carry-save array, one row per bit of B,
+ * then a ripple adder for the upper half (Sec. 4: the significand product is
+ * unrolled and kept in registers). */
+template <int n, class W> BSFP_HD void umul(const W* A, const W* Bv, W* P) {
+    W S[2 * n], C[2 * n];
+    BSFP_UNROLL
+    for (int w = 0; w < 2 * n; ++w) S[w] = C[w] = W(0u);
+    BSFP_UNROLL
+    for (int i = 0; i < n; ++i) S[i] = AND(A[i], Bv[0]);
+    BSFP_UNROLL
+    for (int j = 1; j < n; ++j) {
+        W nc[2 * n];
+        BSFP_UNROLL
+        for (int i = 0; i < n; ++i) {
+            const int w = i + j;
+            const W pp = AND(A[i], Bv[j]);
+            const W s = XOR3(S[w], C[w], pp);
+            nc[w + 1] = MAJ(S[w], C[w], pp);
+            S[w] = s;
+        }
+        C[j] = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < n; ++i) C[i + j + 1] = nc[i + j + 1];
+    }
+    BSFP_UNROLL
+    for (int w = 0; w < n; ++w) P[w] = S[w];
+    W c = W(0u);
+    BSFP_UNROLL
+    for (int w = n; w < 2 * n; ++w) {
+        P[w] = XOR3(S[w], C[w], c);
+        c = MAJ(S[w], C[w], c);
+    }
+}
+
+/* r = a * b, one rounding (Sec. 4, Table 1, Mul). */
+template <int E, int M, bool RZ, class W> BSFP_HD void fp_mul(const W* a, const W* b, W* r) {
+    static_assert(E >= 2 && M >= 1 && 1 + E + M <= 32, "format out of range");
+    constexpr int B = 1 + E + M;
+    constexpr int N1 = M + 1;         /* significand bits */
+    constexpr int NP = 2 * M + 2;     /* product bits */
+    constexpr int NU = E + 2;         /* signed exponent sum */
+    /* step 1: sign */
+    const W s = XOR(a[B - 1], b[B - 1]);
+    const W* ea = a + M;
+    const W* eb = b + M;
+    const W nzA = or_n<E>(ea);
+    const W nzB = or_n<E>(eb);
+
+    /* step 3: significand product */
+    W SA[N1], SB[N1];
+    BSFP_UNROLL
+    for (int i = 0; i < M; ++i) {
+        SA[i] = a[i];
+        SB[i] = b[i];
+    }
+    SA[M] = nzA;
+    SB[M] = nzB;
+    W P[NP];
+    umul<N1>(SA, SB, P);
+
+    /* step 2: u = max(ea,1) + max(eb,1) - bias in NU-bit two's complement,
+     * the two exponent additions merged into one carry-save step + one ripple
+     * (Sec. 4).  u + 1 is the exponent field when the product's top bit
+     * (position 2M+1) is set. */
+    W ua[E], ub[E];
+    ua[0] = OR(ea[0], NOT(nzA));
+    ub[0] = OR(eb[0], NOT(nzB));
+    BSFP_UNROLL
+    for (int i = 1; i < E; ++i) {
+        ua[i] = ea[i];
+        ub[i] = eb[i];
+    }
+    constexpr uint32_t KB = (1u - (1u << (E - 1))) & ((1u << NU) - 1u);  /* -bias + ... : 1 - 2^(E-1) */
+    W u[NU];
+    {
+        W cs[NU], cc[NU + 1];
+        cc[0] = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            const W ai = (i < E) ? ua[(i < E) ? i : 0] : W(0u);
+            const W bi = (i < E) ? ub[(i < E) ? i : 0] : W(0u);
+            const bool k = (KB >> i) & 1u;
+            cs[i] = k ? NOT(XOR(ai, bi)) : XOR(ai, bi);
+            cc[i + 1] = k ? OR(ai, bi) : AND(ai, bi);
+        }
+        W c = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            u[i] = XOR3(cs[i], cc[i], c);
+            if (i + 1 < NU) c = MAJ(cs[i], cc[i], c);
+        }
+    }
+    const W neg = u[NU - 1];   /* u < 0: the product is below the normal range */
+
+    /* step 4a (u >= 0): normalise left by t = min(lz(P), u) */
+    W zl[NP];
+    BSFP_UNROLL
+    for (int i = 0; i < NP; ++i) zl[i] = P[i];
+    W um[NU - 1];
+    BSFP_UNROLL
+    for (int i = 0; i < NU - 1; ++i) um[i] = ANDN(u[i], neg);    /* budget 0 when u < 0 */
+    constexpr int KT = floor_log2(NP - 1);
+    W t[KT + 1];
+    lnorm<NP, NU - 1>(zl, um, t);
+    W D[NU - 1];
+    sub_un<NU - 1, KT + 1>(um, t, D);
+
+    /* step 4b (u < 0): shift right by -u = ~u + 1 with sticky; the top M+2
+     * product bits plus a sticky of the rest suffice.  q[0] sticky, q[1]
+     * guard, q[2..M+2] significand, after the fixed shift by one. */
+    constexpr int NQ = M + 3;
+    W q[NQ];
+    q[0] = or_n<M + 1>(P);
+    BSFP_UNROLL
+    for (int p = 1; p < NQ - 1; ++p) q[p] = P[M + p];
+    q[NQ - 1] = W(0u);
+    if constexpr (E >= 3) {
+        W nu[E - 1];
+        BSFP_UNROLL
+        for (int i = 0; i < E - 1; ++i) nu[i] = NOT(u[i]);
+        rshift_sticky<NQ, E - 1>(q, nu);
+    }
+
+    /* merge the two paths: significand, guard, sticky */
+    W sig[N1];
+    BSFP_UNROLL
+    for (int i = 0; i < N1; ++i) sig[i] = MUX(neg, q[2 + i], zl[M + 1 + i]);
+    W rup = W(0u);
+    if constexpr (!RZ) {
+        const W g = MUX(neg, q[1], zl[M]);
+        const W st = MUX(neg, q[0], or_n<M>(zl));
+        rup = F3<LUT_G_AND_LS>(g, sig[0], st);
+    }
+
+    /* step 5: rounding into the encoded magnitude */
+    W mag[M + NU];
+    assemble<M, NU - 1>(D, sig, rup, mag);
+
+    /* specials: NaN for NaN operands and 0 * Inf; Inf otherwise */
+    const W aspec = and_n<E>(ea), bspec = and_n<E>(eb);
+    const W fA = or_n<M>(a), fB = or_n<M>(b);
+    const W tA = OR(nzA, fA), tB = OR(nzB, fB);     /* operand is nonzero */
+    const W nan = OR(F3<LUT_AND_OR_NOT>(aspec, fA, tB), F3<LUT_AND_OR_NOT>(bspec, fB, tA));
+    const W zero = NOT(AND(tA, tB));
+    encode<E, M, NU, RZ>(mag, OR(aspec, bspec), nan, zero, s, W(0u), r);
+}
+
+/* ----------------------------------------------------------------- ops --- */
+enum Op : int { OP_ADD = 0, OP_SUB = 1, OP_MUL = 2, OP_FMA2 = 3 };
+
+/* r = op(a, b[, c]); fma2 = add(mul(a, b), c), each rounded. */
+template <int E, int M, bool RZ, int OP, class W>
+BSFP_HD void fp_op(const W* a, const W* b, const W* c, W* r) {
+    if constexpr (OP == OP_ADD) {
+        fp_add<E, M, RZ, false>(a, b, r);
+    } else if constexpr (OP == OP_SUB) {
+        fp_add<E, M, RZ, true>(a, b, r);
+    } else if constexpr (OP == OP_MUL) {
+        fp_mul<E, M, RZ>(a, b, r);
+    } else {
+        W p[1 + E + M];
+        fp_mul<E, M, RZ>(a, b, p);
+        fp_add<E, M, RZ, false>(p, c, r);
+    }
+}
+
+}  // namespace bsfp

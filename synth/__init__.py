@@ -57,25 +57,41 @@ def container_dtype(B: int):
     return np.uint8 if B <= 8 else (np.uint16 if B <= 16 else np.uint32)
 
 
+def splitmix64_at(seed: int, idx, stream: int = 0) -> np.ndarray:
+    """Draws at arbitrary counters: element k is draw ``idx[k]`` of the stream."""
+    key = stream_key(seed, stream)
+    i = np.asarray(idx, dtype=np.uint64) + np.uint64(1)
+    with np.errstate(over="ignore"):
+        return _mix(key + i * GAMMA)
+
+
+def _fp_from_draws(E: int, M: int, r: np.ndarray) -> np.ndarray:
+    emax = (1 << E) - 1
+    s = r & np.uint64(1)
+    f = (r >> np.uint64(1)) & np.uint64((1 << M) - 1)
+    h = r >> np.uint64(32)
+    t = h % np.uint64(100)
+    e = np.uint64(1) + (h // np.uint64(100)) % np.uint64(emax - 1)
+    e = np.where(t == 0, np.uint64(0), np.where(t == 1, np.uint64(emax), e))
+    return (s << np.uint64(E + M)) | (e << np.uint64(M)) | f
+
+
 def fp_values(E: int, M: int, n: int, seed: int, stream: int = 0, start: int = 0,
               dtype=None) -> np.ndarray:
     """``n`` B-bit patterns of format 1/E/M with the recipe in the module doc."""
     B = 1 + E + M
     dtype = dtype or container_dtype(B)
     out = np.empty(n, dtype=dtype)
-    emax = (1 << E) - 1
     for lo in range(0, n, _CHUNK):
         hi = min(n, lo + _CHUNK)
         r = splitmix64(seed, hi - lo, stream, start + lo)
-        s = r & np.uint64(1)
-        f = (r >> np.uint64(1)) & np.uint64((1 << M) - 1)
-        h = r >> np.uint64(32)
-        t = h % np.uint64(100)
-        e = np.uint64(1) + (h // np.uint64(100)) % np.uint64(emax - 1)
-        e = np.where(t == 0, np.uint64(0), np.where(t == 1, np.uint64(emax), e))
-        v = (s << np.uint64(E + M)) | (e << np.uint64(M)) | f
-        out[lo:hi] = v.astype(dtype)
+        out[lo:hi] = _fp_from_draws(E, M, r).astype(dtype)
     return out
+
+
+def fp_values_at(E: int, M: int, idx, seed: int, stream: int = 0) -> np.ndarray:
+    """The values ``fp_values`` gives at the element indices ``idx`` (uint32)."""
+    return _fp_from_draws(E, M, splitmix64_at(seed, idx, stream)).astype(np.uint32)
 
 
 def uniform_bits(B: int, n: int, seed: int, stream: int = 0, dtype=None) -> np.ndarray:

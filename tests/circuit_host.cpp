@@ -1,0 +1,53 @@
+/* Test harness: evaluates the bitslice circuits of the CUDA library's
+ * circuit.cuh on the host with 32-bit words, so that the circuit logic can be
+ * compared with the oracle on a CPU (the GPU parity tests run the same
+ * templates inside the kernels).  Test infrastructure only; nothing in the
+ * library calls it.  Built by tests/_helpers.py with g++. */
+#include <stdint.h>
+
+#include "circuit.cuh"
+
+using namespace bsfp;
+
+template <int E, int M, bool RZ, int OP>
+static void run(const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out, long nwords, long S) {
+    constexpr int B = 1 + E + M;
+    for (long w = 0; w < nwords; ++w) {
+        uint32_t x[B], y[B], z[B], r[B];
+        for (int i = 0; i < B; ++i) {
+            x[i] = a[i * S + w];
+            y[i] = b[i * S + w];
+            z[i] = c[i * S + w];
+        }
+        fp_op<E, M, RZ, OP>(x, y, z, r);
+        for (int i = 0; i < B; ++i) out[i * S + w] = r[i];
+    }
+}
+
+template <int E, int M>
+static int dispatch_fmt(int rz, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
+                        long nwords, long S) {
+    switch (op * 2 + (rz ? 1 : 0)) {
+        case 0: run<E, M, false, OP_ADD>(a, b, c, out, nwords, S); return 0;
+        case 1: run<E, M, true, OP_ADD>(a, b, c, out, nwords, S); return 0;
+        case 2: run<E, M, false, OP_SUB>(a, b, c, out, nwords, S); return 0;
+        case 3: run<E, M, true, OP_SUB>(a, b, c, out, nwords, S); return 0;
+        case 4: run<E, M, false, OP_MUL>(a, b, c, out, nwords, S); return 0;
+        case 5: run<E, M, true, OP_MUL>(a, b, c, out, nwords, S); return 0;
+        case 6: run<E, M, false, OP_FMA2>(a, b, c, out, nwords, S); return 0;
+        case 7: run<E, M, true, OP_FMA2>(a, b, c, out, nwords, S); return 0;
+    }
+    return -1;
+}
+
+#define FMT(E, M) \
+    if (e == E && m == M) return dispatch_fmt<E, M>(rz, op, a, b, c, out, nwords, S);
+
+extern "C" int host_circuit(int e, int m, int rz, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                            uint32_t* out, long nwords, long S) {
+    /* the formats the CPU tests exercise */
+    FMT(2, 1) FMT(2, 3) FMT(3, 2) FMT(3, 3) FMT(2, 5) FMT(3, 4) FMT(4, 3) FMT(5, 2) FMT(4, 4) FMT(5, 4)
+    FMT(4, 5) FMT(5, 7) FMT(5, 10) FMT(8, 7) FMT(8, 23) FMT(3, 23) FMT(8, 2) FMT(6, 9) FMT(7, 13)
+    FMT(2, 23) FMT(8, 1) FMT(3, 12)
+    return -1;
+}

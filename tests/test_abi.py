@@ -1,0 +1,122 @@
+"""The C ABI without a GPU: the library loads, exports every function the
+public headers declare, and its host-side logic (sizes, validation, status
+strings, gate counts) behaves as documented.  No call here reaches a kernel
+launch: every failing call is rejected by validation first."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1602_04716_gb300 as bs
+from paper_1602_04716_gb300 import bsfp as _binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(INCLUDE):
+        if h.endswith(".h"):
+            text = open(os.path.join(INCLUDE, h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(bsfp_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_function():
+    L = ctypes.CDLL(bs.lib_path())
+    names = _declared()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_plane_stride_and_sizes():
+    assert bs.bsfp_plane_stride(0) == 0
+    assert bs.bsfp_plane_stride(1) == 32
+    assert bs.bsfp_plane_stride(1024) == 32
+    assert bs.bsfp_plane_stride(1025) == 64
+    assert bs.bsfp_plane_stride(1 << 28) == 1 << 23
+    assert bs.bsfp_plane_stride(-1) == -1
+    f = bs.Format(5, 7)
+    assert bs.bsfp_bitslice_bytes(f, 1 << 28) == 13 * (1 << 23) * 4
+    assert bs.bsfp_container_bytes(bs.Format(4, 3)) == 1
+    assert bs.bsfp_container_bytes(bs.Format(4, 4)) == 2
+    assert bs.bsfp_container_bytes(bs.Format(5, 10)) == 2
+    assert bs.bsfp_container_bytes(bs.Format(8, 23)) == 4
+    assert bs.bsfp_container_bytes(bs.Format(9, 7)) == -1
+
+
+@pytest.mark.parametrize("fmt", [(1, 3, 0), (9, 3, 0), (4, 0, 0), (4, 24, 0), (4, 3, 2), (4, 3, -1)])
+def test_bad_format_rejected(fmt):
+    f = bs.Format(*fmt)
+    L = _binding._lib()
+    assert L.bsfp_add(f, 256, 256, 256, 10, None) == bs.ERR_FORMAT
+    assert L.bsfp_pack(f, 256, 10, 256, None) == bs.ERR_FORMAT
+    assert L.bsfp_bitslice_bytes(f, 10) == -1
+    assert L.bsfp_gate_count(f, 0) == -1
+
+
+def test_validation_order_and_codes():
+    L = _binding._lib()
+    f = bs.Format(5, 7)
+    assert L.bsfp_add(f, 256, 256, 256, -1, None) == bs.ERR_SIZE
+    assert L.bsfp_add(f, 256, 256, 256, bs.MAX_N + 1, None) == bs.ERR_SIZE
+    assert L.bsfp_add(f, None, 256, 256, 10, None) == bs.ERR_NULL
+    assert L.bsfp_fma2(f, 256, 256, None, 256, 10, None) == bs.ERR_NULL
+    assert L.bsfp_mul(f, 264, 256, 256, 10, None) == bs.ERR_ALIGN
+    assert L.bsfp_sub(f, 256, 256, 260, 10, None) == bs.ERR_ALIGN
+    assert L.bsfp_pack(f, 257, 10, 256, None) == bs.ERR_ALIGN       # uint16 container, odd address
+    assert L.bsfp_unpack(f, 256, 10, 257, None) == bs.ERR_ALIGN
+    assert L.bsfp_unpack(f, 264, 10, 256, None) == bs.ERR_ALIGN
+    # n == 0 is valid and launches nothing, whatever the pointers
+    for fn in (L.bsfp_add, L.bsfp_sub, L.bsfp_mul):
+        assert fn(f, None, None, None, 0, None) == bs.OK
+    assert L.bsfp_fma2(f, None, None, None, None, 0, None) == bs.OK
+    assert L.bsfp_pack(f, None, 0, None, None) == bs.OK
+    assert L.bsfp_unpack(f, None, 0, None, None) == bs.OK
+
+
+def test_status_strings():
+    for code in range(0, -9, -1):
+        s = bs.status_str(code)
+        assert s and s != "unknown status"
+    assert bs.status_str(-100) == "unknown status"
+
+
+def test_variants_and_overrides():
+    f = bs.Format(5, 7)
+    assert bs.bsfp_variants_compiled(f, "add") == [1, 2, 4]
+    assert bs.bsfp_variant(f, "add") in (1, 2, 4)
+    g = bs.Format(6, 9)
+    assert len(bs.bsfp_variants_compiled(g, "mul")) == 1
+    with pytest.raises(bs.BsfpError):
+        bs.bsfp_set_variant(g, "mul", 4)
+    bs.bsfp_set_variant(f, "mul", 1, 3)
+    assert bs.bsfp_variant(f, "mul") == 1
+    bs.bsfp_set_variant(f, "mul", 2, 0)
+    assert bs.bsfp_variant(f, "mul") == 2
+    # every format in range is compiled for every op
+    for e in range(2, 9):
+        for m in range(1, 24):
+            for op in range(4):
+                assert bs.bsfp_variants_compiled(bs.Format(e, m), op), (e, m, op)
+
+
+def test_gate_counts_follow_table1_classes():
+    """Sec. 4, Table 1: add/sub is O(n log n) in the significand width and mul
+    O(n^2).  Over M = 7 -> 23 at E = 8 the multiplier must grow much faster
+    than the adder, and sub costs the same as add (one folded inversion)."""
+    g = lambda e, m, op, r=0: bs.bsfp_gate_count(bs.Format(e, m, r), op)
+    add7, add23 = g(8, 7, "add"), g(8, 23, "add")
+    mul7, mul23 = g(8, 7, "mul"), g(8, 23, "mul")
+    assert add23 / add7 < 3.0
+    assert mul23 / mul7 > 4.0
+    assert g(5, 7, "sub") == g(5, 7, "add")
+    assert g(5, 7, "fma2") <= g(5, 7, "add") + g(5, 7, "mul")
+    # RZ drops the round-up logic, so it never costs more than RN (Sec. 5.2)
+    for e, m in [(4, 3), (5, 10), (8, 23)]:
+        for op in ("add", "mul"):
+            assert g(e, m, op, 1) <= g(e, m, op, 0)

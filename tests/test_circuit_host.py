@@ -1,0 +1,103 @@
+"""The library's circuit templates (circuit.cuh) evaluated on the host with
+32-bit words, compared bit for bit with the oracle.  This exercises the same
+gate-level code the CUDA kernels run, without a GPU: exhaustively over every
+operand pair for formats of at most 8 bits and on seeded samples for wider
+formats, for add, sub, mul and fma2 under RN and RZ."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1602_04716_gb300", "csrc")
+OPS = ["add", "sub", "mul", "fma2"]
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        out = os.path.join(tempfile.gettempdir(), "bsfp_circuit_host_%d.so" % os.getpid())
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-I", CSRC, "-o", out,
+                               os.path.join(HERE, "circuit_host.cpp")])
+        L = ctypes.CDLL(out)
+        L.host_circuit.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 4 + [ctypes.c_long] * 2
+        L.host_circuit.restype = ctypes.c_int
+        _L = L
+    return _L
+
+
+def circuit(E, M, rnd, op, a, b, c=None):
+    """Pack with the oracle's bit loop, run the circuit, unpack."""
+    B = 1 + E + M
+    a = np.asarray(a, np.uint32)
+    b = np.asarray(b, np.uint32)
+    c = np.zeros_like(a) if c is None else np.asarray(c, np.uint32)
+    pa, pb, pc = oracle.pack(B, a), oracle.pack(B, b), oracle.pack(B, c)
+    S = pa.shape[1]
+    out = np.zeros_like(pa)
+    rc = _lib().host_circuit(E, M, rnd, OPS.index(op), pa.ctypes.data, pb.ctypes.data, pc.ctypes.data,
+                             out.ctypes.data, S, S)
+    assert rc == 0, "format not in the host harness"
+    return oracle.unpack(B, out, a.size)
+
+
+def _first_bad(got, want, *ins):
+    bad = np.nonzero(got != want)[0]
+    if not len(bad):
+        return ""
+    i = bad[0]
+    return "%d mismatches; first at %d: in=%s got=%#x want=%#x" % (
+        len(bad), i, [hex(int(x[i])) for x in ins], got[i], want[i])
+
+
+SMALL = [(2, 1), (2, 3), (3, 2), (3, 3), (2, 5), (3, 4), (4, 3), (5, 2)]
+
+
+@pytest.mark.parametrize("E,M", SMALL)
+@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_circuit_exhaustive_small(E, M, op, rnd):
+    a, b = synth.all_pairs(1 + E + M)
+    a, b = a.astype(np.uint32), b.astype(np.uint32)
+    got = circuit(E, M, rnd, op, a, b)
+    want = oracle.binop(op, E, M, rnd, a, b)
+    assert (got == want).all(), _first_bad(got, want, a, b)
+
+
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_circuit_fma2_1_4_3_sampled(rnd):
+    n = 1 << 18
+    a = synth.uniform_bits(8, n, 11).astype(np.uint32)
+    b = synth.uniform_bits(8, n, 12).astype(np.uint32)
+    c = synth.uniform_bits(8, n, 13).astype(np.uint32)
+    got = circuit(4, 3, rnd, "fma2", a, b, c)
+    want = oracle.fma2(4, 3, rnd, a, b, c)
+    assert (got == want).all(), _first_bad(got, want, a, b, c)
+
+
+WIDE = [(4, 4), (5, 4), (4, 5), (5, 7), (5, 10), (8, 7), (8, 23), (3, 23), (8, 2), (6, 9), (7, 13),
+        (2, 23), (8, 1), (3, 12)]
+
+
+@pytest.mark.parametrize("E,M", WIDE)
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_circuit_wide_sampled(E, M, rnd):
+    n = 1 << 15
+    B = 1 + E + M
+    for gen in ("fp", "bits"):
+        if gen == "fp":
+            a, b, c = (synth.fp_values(E, M, n, s).astype(np.uint32) for s in (21, 22, 23))
+        else:
+            a, b, c = (synth.uniform_bits(B, n, s).astype(np.uint32) for s in (31, 32, 33))
+        for op in OPS:
+            got = circuit(E, M, rnd, op, a, b, c)
+            want = oracle.binop(op, E, M, rnd, a, b, c)
+            assert (got == want).all(), "%s %s: %s" % (gen, op, _first_bad(got, want, a, b, c))

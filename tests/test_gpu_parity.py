@@ -1,0 +1,303 @@
+"""Parity of the CUDA path with the oracle, bit for bit, through the C ABI.
+
+Every result is integer logic, so the bar is exact equality of encodings and
+of whole plane buffers (padding included).  Operands for the op tests are
+packed by the oracle on the host, so each kernel is checked on its own:
+pack and unpack against the oracle's bit loops, each op against the oracle's
+exact-then-round arithmetic.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_1602_04716_gb300 as bs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+OPS = ["add", "sub", "mul", "fma2"]
+RNDS = [oracle.RN, oracle.RZ]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------ helpers ---
+def dev(x: np.ndarray):
+    x = np.ascontiguousarray(x)
+    view = {1: np.uint8, 2: np.int16, 4: np.int32}[x.dtype.itemsize]
+    return torch.from_numpy(x.view(view).copy()).cuda()
+
+
+def host_u32(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
+
+
+def gpu_op(op, E, M, rnd, a, b, c=None, wpt=None, bps=0):
+    """Oracle-packed operands -> GPU op -> planes (B, S) on the host."""
+    B = 1 + E + M
+    f = bs.Format(E, M, rnd)
+    n = len(a)
+    pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+    pc = dev(oracle.pack(B, c)) if c is not None else None
+    out = torch.full_like(pa, -1)
+    if wpt is not None:
+        bs.bsfp_set_variant(f, op, wpt, bps)
+    bs.bsfp_op(op, f, pa, pb, out, n, c=pc)
+    torch.cuda.synchronize()
+    return host_u32(out).reshape(B, -1)
+
+
+def want_planes(op, E, M, rnd, a, b, c=None):
+    B = 1 + E + M
+    return oracle.pack(B, oracle.binop(op, E, M, rnd, a, b, c))
+
+
+def describe(got, want, B, n, *ins):
+    if (got == want).all():
+        return ""
+    g = oracle.unpack(B, got, n)
+    w = oracle.unpack(B, want, n)
+    bad = np.nonzero(g != w)[0]
+    if not len(bad):
+        return "padding differs"
+    i = bad[0]
+    return "%d/%d mismatches; first at %d: in=%s got=%#x want=%#x" % (
+        len(bad), n, i, [hex(int(x[i])) for x in ins if x is not None], g[i], w[i])
+
+
+def check(op, E, M, rnd, a, b, c=None, **kw):
+    B = 1 + E + M
+    a = np.asarray(a, np.uint32)
+    b = np.asarray(b, np.uint32)
+    c = None if c is None else np.asarray(c, np.uint32)
+    if op == "fma2" and c is None:
+        c = synth.fp_values(E, M, len(a), 99).astype(np.uint32)
+    got = gpu_op(op, E, M, rnd, a, b, c, **kw)
+    want = want_planes(op, E, M, rnd, a, b, c)
+    assert (got == want).all(), "%s 1/%d/%d rnd=%d: %s" % (op, E, M, rnd, describe(got, want, B, len(a), a, b, c))
+
+
+# ------------------------------------------------------ pack / unpack ---
+SIZES = [1, 31, 32, 33, 1023, 1024, 1025, 4097, 65537, 100003]
+
+
+@pytest.mark.parametrize("E,M", [(4, 3), (2, 1), (4, 4), (5, 10), (8, 7), (8, 23), (3, 12), (6, 17)])
+@pytest.mark.parametrize("n", SIZES)
+def test_pack_unpack_vs_oracle(E, M, n):
+    B = 1 + E + M
+    f = bs.Format(E, M)
+    cb = bs.bsfp_container_bytes(f)
+    cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[cb]
+    # containers carry junk above bit B: pack must ignore it
+    raw = synth.uniform_bits(8 * cb, n, 7 + B, dtype=cdt)
+    x = (raw.astype(np.uint64) & ((1 << B) - 1)).astype(np.uint32)
+    planes = torch.full((B * bs.bsfp_plane_stride(n),), -1, dtype=torch.int32, device="cuda")
+    bs.bsfp_pack(f, dev(raw), n, planes)
+    back = torch.full((n,), -1, dtype=bs.container_dtype(f), device="cuda")
+    bs.bsfp_unpack(f, planes, n, back)
+    torch.cuda.synchronize()
+    got_planes = host_u32(planes).reshape(B, -1)
+    want_planes_ = oracle.pack(B, x)
+    assert (got_planes == want_planes_).all(), "pack differs from the oracle"
+    got = back.cpu().numpy().view(cdt).astype(np.uint32)
+    assert (got == x).all(), "unpack(pack(x)) != x"
+
+
+def test_unpack_of_oracle_planes():
+    E, M, n = 5, 7, 70001
+    x = synth.fp_values(E, M, n, 3).astype(np.uint32)
+    planes = dev(oracle.pack(13, x))
+    out = torch.empty(n, dtype=torch.int16, device="cuda")
+    bs.bsfp_unpack(bs.Format(E, M), planes, n, out)
+    assert (out.cpu().numpy().view(np.uint16).astype(np.uint32) == oracle.unpack(13, oracle.pack(13, x), n)).all()
+
+
+# --------------------------------------------------- exhaustive small ---
+SMALL = [(2, 1), (2, 3), (3, 2), (3, 3), (2, 5), (3, 4), (4, 3), (5, 2)]
+
+
+@pytest.mark.parametrize("E,M", SMALL)
+@pytest.mark.parametrize("rnd", RNDS)
+def test_exhaustive_pairs_small_formats(E, M, rnd):
+    a, b = synth.all_pairs(1 + E + M)
+    for op in ("add", "sub", "mul"):
+        check(op, E, M, rnd, a, b)
+
+
+@pytest.mark.parametrize("rnd", RNDS)
+def test_exhaustive_pairs_1_4_4(rnd):
+    a, b = synth.all_pairs(9)
+    for op in ("add", "sub", "mul"):
+        check(op, 4, 4, rnd, a, b)
+
+
+@pytest.mark.parametrize("rnd", RNDS)
+def test_fma2_exhaustive_triples_1_4_3(rnd):
+    i = np.arange(1 << 24, dtype=np.uint32)
+    a, b, c = i >> 16, (i >> 8) & 255, i & 255
+    check("fma2", 4, 3, rnd, a, b, c)
+
+
+# ------------------------------------------------ every compiled format ---
+@pytest.mark.parametrize("E", range(2, 9))
+def test_every_format_every_op(E):
+    """Each of the 23 formats 1/E/1 .. 1/E/23, four ops, both roundings, on
+    seeded values of the workload recipe plus uniformly random encodings, at a
+    length with a ragged tail."""
+    n = 5000 + 17 * E
+    for M in range(1, 24):
+        B = 1 + E + M
+        a = np.concatenate([synth.fp_values(E, M, n, 1000 + M).astype(np.uint32),
+                            synth.uniform_bits(B, n, 2000 + M).astype(np.uint32)])
+        b = np.concatenate([synth.fp_values(E, M, n, 3000 + M).astype(np.uint32),
+                            synth.uniform_bits(B, n, 4000 + M).astype(np.uint32)])
+        c = np.concatenate([synth.fp_values(E, M, n, 5000 + M).astype(np.uint32),
+                            synth.uniform_bits(B, n, 6000 + M).astype(np.uint32)])
+        for rnd in RNDS:
+            for op in OPS:
+                check(op, E, M, rnd, a, b, c if op == "fma2" else None)
+
+
+TUNED = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]
+
+
+@pytest.mark.parametrize("E,M", TUNED)
+def test_every_launch_variant(E, M):
+    n = 200_000 + 13
+    a, b, c = (synth.fp_values(E, M, n, s).astype(np.uint32) for s in (41, 42, 43))
+    for op in OPS:
+        f = bs.Format(E, M, oracle.RN)
+        for wpt in bs.bsfp_variants_compiled(f, op):
+            for bps in (0, 1):
+                check(op, E, M, oracle.RN, a, b, c if op == "fma2" else None, wpt=wpt, bps=bps)
+        bs.bsfp_set_variant(f, op, 0, 0)
+
+
+# ------------------------------------------------------------ edge cases ---
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1023, 1025, 32 * 1024 - 1, 32 * 1024 + 1])
+def test_tail_lengths(n):
+    E, M = 5, 7
+    a, b, c = (synth.fp_values(E, M, n, s).astype(np.uint32) for s in (51, 52, 53))
+    for op in OPS:
+        check(op, E, M, oracle.RN, a, b, c if op == "fma2" else None)
+
+
+def test_padding_written_as_zero_whatever_the_inputs_hold():
+    E, M, n = 4, 4, 1000
+    B = 9
+    f = bs.Format(E, M)
+    S = bs.bsfp_plane_stride(n)
+    a = synth.fp_values(E, M, n, 61).astype(np.uint32)
+    b = synth.fp_values(E, M, n, 62).astype(np.uint32)
+    pa, pb = oracle.pack(B, a), oracle.pack(B, b)
+    junk = synth.uniform_bits(32, B * S, 63, dtype=np.uint32).reshape(B, S)
+    nw = (n + 31) // 32
+    tail = np.uint32((1 << (n % 32)) - 1)
+    for p in (pa, pb):
+        p[:, nw:] = junk[:, nw:]
+        p[:, nw - 1] |= junk[:, nw - 1] & ~tail
+    for op in ("add", "mul"):
+        out = torch.full((B * S,), -1, dtype=torch.int32, device="cuda")
+        bs.bsfp_op(op, f, dev(pa), dev(pb), out, n)
+        got = host_u32(out).reshape(B, S)
+        assert (got == oracle.pack(B, oracle.binop(op, E, M, 0, a, b))).all()
+
+
+def test_output_may_alias_an_input():
+    E, M, n = 5, 10, 77777
+    B = 16
+    f = bs.Format(E, M)
+    a = synth.fp_values(E, M, n, 71).astype(np.uint32)
+    b = synth.fp_values(E, M, n, 72).astype(np.uint32)
+    for op in ("add", "sub", "mul"):
+        ta, tb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+        bs.bsfp_op(op, f, ta, tb, ta, n)
+        assert (host_u32(ta).reshape(B, -1) == want_planes(op, E, M, 0, a, b)).all(), op
+
+
+def test_empty_vector_launches_nothing():
+    before = bs.bsfp_launch_count()
+    f = bs.Format(5, 7)
+    t = torch.zeros(64, dtype=torch.int32, device="cuda")
+    for op in ("add", "sub", "mul"):
+        bs.bsfp_op(op, f, t, t, t, 0)
+    bs.bsfp_pack(f, t, 0, t)
+    assert bs.bsfp_launch_count() == before
+
+
+def test_streams_are_respected():
+    E, M, n = 5, 7, 1 << 20
+    B = 13
+    f = bs.Format(E, M)
+    a = synth.fp_values(E, M, n, 81).astype(np.uint32)
+    b = synth.fp_values(E, M, n, 82).astype(np.uint32)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ta, tb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+        out = torch.empty_like(ta)
+        bs.bsfp_mul(f, ta, tb, out, n, stream=s)
+    s.synchronize()
+    assert (host_u32(out).reshape(B, -1) == want_planes("mul", E, M, 0, a, b)).all()
+
+
+# ---------------------------------------------------- input generator ---
+@pytest.mark.parametrize("E,M", [(4, 3), (4, 4), (5, 7), (8, 23), (3, 2)])
+def test_device_generator_matches_host(E, M):
+    f = bs.Format(E, M)
+    n, start = 100_003, 12345
+    out = bs.empty_standard(f, n)
+    bs.bsfp_synth_fp_values(f, n, 1602, 3, start, out)
+    cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[bs.bsfp_container_bytes(f)]
+    got = out.cpu().numpy().view(cdt)
+    assert (got == synth.fp_values(E, M, n, 1602, 3, start, dtype=cdt)).all()
+
+
+def test_lop3_probe_runs():
+    sink = torch.zeros(4 * 256, dtype=torch.int32, device="cuda")
+    bs.bsfp_lop3_probe(sink, 4, 256, 10)
+    torch.cuda.synchronize()
+    assert int((sink != 0).sum()) > 0
+
+
+# -------------------------------------------- full size, sampled outputs ---
+@pytest.mark.parametrize("E,M", [(4, 4), (5, 7)])
+def test_full_size_2_28_sampled(E, M):
+    """The benchmark's workload: 2^28 elements generated on the device, packed,
+    added and multiplied with the launch shape the benchmark uses; 2^16
+    sampled outputs (and the last element) against the oracle."""
+    from bench import apply_tuning
+    apply_tuning()
+    n = 1 << 28
+    f = bs.Format(E, M)
+    B = 1 + E + M
+    std = bs.empty_standard(f, n)
+    planes = []
+    for seed in (synth.SEED_A, synth.SEED_B):
+        bs.bsfp_synth_fp_values(f, n, seed, 0, 0, std)
+        p = bs.empty_bitslice(f, n)
+        bs.bsfp_pack(f, std, n, p)
+        planes.append(p)
+    out = bs.empty_bitslice(f, n)
+    rng = np.random.default_rng(E * 100 + M)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 1 << 16), [0, n - 1]])).astype(np.int64)
+    xa = synth.fp_values_at(E, M, idx, synth.SEED_A)
+    xb = synth.fp_values_at(E, M, idx, synth.SEED_B)
+    cdt = np.uint16
+    idx_t = torch.from_numpy(idx).cuda()
+    for op in ("add", "mul"):
+        bs.bsfp_op(op, f, planes[0], planes[1], out, n)
+        bs.bsfp_unpack(f, out, n, std)
+        got = std[idx_t].cpu().numpy().view(cdt).astype(np.uint32)
+        want = oracle.binop(op, E, M, 0, xa, xb)
+        bad = np.nonzero(got != want)[0]
+        assert not len(bad), "%s: %d bad, first idx %d" % (op, len(bad), idx[bad[0]])
+    del planes, out, std
+    torch.cuda.empty_cache()
