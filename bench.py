@@ -306,6 +306,10 @@ def run_gpu(args):
     if not args.no_e2e:
         e2e = run_e2e(bs, torch, n, rank, args)
 
+    batched = None
+    if args.batch_jobs > 0:
+        batched = run_batched(bs, torch, args, rank, hbm)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -320,12 +324,87 @@ def run_gpu(args):
                            "seeds": [synth.SEED_A, synth.SEED_B], "parallelism": "dp%d" % world,
                            "tuned_shapes_applied": tuned},
                 "roofline": roof, "kernels": kinfo, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, "batched": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+BATCH_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
+
+
+def batched_workload(bs, torch, njobs, lo, hi, seed, rank=0, formats=BATCH_FORMATS, ops=("add", "mul")):
+    """njobs independent vectors: lengths log-uniform in [lo, hi], formats
+    uniform over `formats`, ops uniform over `ops`, RN; operands drawn on the
+    device and packed.  Returns (ctypes job array, njobs, tensors, elements,
+    algorithmic bytes)."""
+    lens = synth.log_uniform_lengths(njobs, lo, hi, seed, 2 * rank)
+    r = synth.splitmix64(seed, 2 * njobs, 2 * rank + 1)
+    std = {}
+    specs, keep, elems, nbytes = [], [], 0, 0
+    for i in range(njobs):
+        E, M = formats[int(r[2 * i] % len(formats))]
+        op = ops[int(r[2 * i + 1] % len(ops))]
+        n = int(lens[i])
+        f = bs.Format(E, M, RND)
+        if (E, M) not in std:
+            std[(E, M)] = bs.empty_standard(f, hi)
+        planes = []
+        for k in range(2):
+            bs.bsfp_synth_fp_values(f, n, seed + 7919 * i + k, rank, 0, std[(E, M)])
+            p = bs.empty_bitslice(f, n)
+            bs.bsfp_pack(f, std[(E, M)], n, p)
+            planes.append(p)
+        out = bs.empty_bitslice(f, n)
+        specs.append((f, op, planes[0], planes[1], None, out, n))
+        keep += planes + [out]
+        elems += n
+        nbytes += 3 * (1 + E + M) * n / 8
+    torch.cuda.synchronize()
+    arr, nj = bs.make_jobs(specs)
+    return arr, nj, keep, elems, nbytes
+
+
+def run_batched(bs, torch, args, rank, hbm):
+    """Batched persistent launch vs per-vector plain launches on one mixed
+    workload (4,096 vectors, lengths log-uniform in [1,024, 4,194,304],
+    formats uniform over the five batched formats, add/mul 50/50)."""
+    arr, nj, keep, elems, nbytes = batched_workload(bs, torch, args.batch_jobs, 1024, 1 << 22, 20160216, rank)
+    stream = torch.cuda.current_stream()
+    res = {"workload": "%d vectors, lengths log-uniform in [1024, 4194304], formats %s uniform, add/mul 50/50, RN"
+                       % (nj, ["1/%d/%d" % fm for fm in BATCH_FORMATS]),
+           "elements_per_step": elems, "algorithmic_bytes_per_step": nbytes}
+
+    def timed(fn, steps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = bs.bsfp_launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, (bs.bsfp_launch_count() - l0) // steps
+
+    variants = {}
+    persistent = bs.BatchPlan(arr, nj, bs.BATCH_PERSISTENT, args.batch_wpt)
+    variants["persistent_graph"] = timed(lambda: persistent.run(stream), args.batch_steps)
+    plain_graph = bs.BatchPlan(arr, nj, bs.BATCH_PLAIN)
+    variants["plain_graph"] = timed(lambda: plain_graph.run(stream), args.batch_steps)
+    variants["plain_launches"] = timed(lambda: bs.bsfp_launch_jobs(arr, nj, stream), args.batch_steps)
+    for k, (ms, launches) in variants.items():
+        res[k] = {"ms_per_step": ms, "elements_per_s": elems / (ms * 1e-3), "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
+                  "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "launches_per_step": launches}
+    res["speedup_vs_plain_graph"] = variants["plain_graph"][0] / variants["persistent_graph"][0]
+    res["speedup_vs_plain_launches"] = variants["plain_launches"][0] / variants["persistent_graph"][0]
+    persistent.free()
+    plain_graph.free()
+    del keep
+    return res
 
 
 def run_e2e(bs, torch, n, rank, args):
@@ -400,6 +479,10 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=1 << 20,
                     help="reference arm: elements per vector per step")
+    ap.add_argument("--batch-jobs", type=int, default=4096,
+                    help="vectors in the batched comparison (0 skips it)")
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-wpt", type=int, default=0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

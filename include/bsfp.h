@@ -113,6 +113,60 @@ bsfp_status bsfp_mul(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32
 bsfp_status bsfp_fma2(bsfp_format f, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
                       int64_t n, bsfp_stream_t s);
 
+/* -------------------------------------------------------------- batched --- */
+/* One element-wise op on one vector: the unit of a batch.  c is used by
+ * BSFP_OP_FMA2 only.  Same pointer, alignment and n rules as the single ops. */
+typedef struct {
+    bsfp_format f;
+    int32_t op;          /* bsfp_op */
+    const uint32_t* a;
+    const uint32_t* b;
+    const uint32_t* c;
+    uint32_t* out;
+    int64_t n;
+} bsfp_job;
+
+typedef struct bsfp_batch_plan_st* bsfp_batch_plan;
+
+typedef enum {
+    BSFP_BATCH_PERSISTENT = 0, /* one persistent kernel per op class over all tiles */
+    BSFP_BATCH_PLAIN = 1       /* one plain kernel launch per job, captured in the graph */
+} bsfp_batch_mode;
+
+/* Launch shape of a plan.  wpt: words per thread in the persistent kernels
+ * (1 or 2; 0 = 2).  blocks_per_sm: resident CTAs per SM for them (0 = the
+ * occupancy maximum). */
+typedef struct {
+    int32_t mode;          /* bsfp_batch_mode */
+    int32_t wpt;
+    int32_t blocks_per_sm;
+} bsfp_batch_options;
+
+/* Build a plan for njobs independent jobs (not part of the paper: a batched
+ * form of the Sec. 4 operations for many vectors of mixed formats).  Jobs
+ * whose format is 1/4/3, 1/4/4, 1/5/7, 1/5/10 or 1/8/7 go to the persistent
+ * kernels (one per op class: add/sub, mul, fma2; tiles handed out by an
+ * atomic counter); any other compiled format runs as its plain kernel in the
+ * same graph.  The plan owns a device buffer (job descriptors, the tile-to-
+ * job map and the counters, allocated here) and a CUDA graph capturing
+ * counter reset + kernels; it keeps the job pointers, which must stay valid
+ * while the plan is run.  opt may be NULL.  Validation errors (any job)
+ * return before anything is allocated.  Synchronous w.r.t. the host (it
+ * uploads the descriptors). */
+bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bsfp_batch_options* opt,
+                                   bsfp_batch_plan* plan_out);
+/* Launch the plan's graph on stream s.  Runs of one plan must not overlap on
+ * the GPU (they share the tile counters): use one stream per plan. */
+bsfp_status bsfp_batch_run(bsfp_batch_plan plan, bsfp_stream_t s);
+/* Kernel launches one run of the plan performs. */
+int64_t bsfp_batch_launches(bsfp_batch_plan plan);
+/* Release the plan; the caller must make sure no run of it is in flight. */
+void bsfp_batch_free(bsfp_batch_plan plan);
+/* The comparator: every job as its own plain kernel launch on stream s, no
+ * graph, no allocation.  Stops at the first invalid job (jobs before it are
+ * already queued). */
+bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s);
+
 /* ---------------------------------------------------------- diagnostics --- */
 const char* bsfp_status_str(int32_t status);
 /* The cudaError_t of the last BSFP_ERR_CUDA on this thread (0 if none). */

@@ -51,6 +51,20 @@ class bsfp_format(ctypes.Structure):
 
 Format = bsfp_format
 
+
+class bsfp_job(ctypes.Structure):
+    """One element-wise op on one vector (a unit of a batch)."""
+    _fields_ = [("f", bsfp_format), ("op", ctypes.c_int32), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("c", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class bsfp_batch_options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("wpt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+BATCH_PERSISTENT, BATCH_PLAIN = 0, 1
+BATCH_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
+
 _lock = threading.Lock()
 _L = None
 
@@ -87,6 +101,12 @@ def _lib():
                 "bsfp_synth_fp_values": (i32, [F, i64, u64, u64, i64, p, p]),
                 "bsfp_lop3_probe": (i32, [p, i32, i32, i32, u32, p]),
                 "bsfp_num_sms": (i32, []),
+                "bsfp_batch_plan_create": (i32, [ctypes.POINTER(bsfp_job), i32, ctypes.POINTER(bsfp_batch_options),
+                                                 ctypes.POINTER(p)]),
+                "bsfp_batch_run": (i32, [p, p]),
+                "bsfp_batch_launches": (i64, [p]),
+                "bsfp_batch_free": (None, [p]),
+                "bsfp_launch_jobs": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -206,6 +226,53 @@ def bsfp_set_variant(f, op, wpt: int, blocks_per_sm: int = 0):
 
 def bsfp_launch_count() -> int:
     return int(_lib().bsfp_launch_count())
+
+
+# -------------------------------------------------------------- batched ---
+def make_jobs(specs):
+    """specs: iterable of (format, op, a, b, c, out, n) -> ctypes array of bsfp_job."""
+    specs = list(specs)
+    arr = (bsfp_job * max(1, len(specs)))()
+    for i, (f, op, a, b, c, out, n) in enumerate(specs):
+        arr[i] = bsfp_job(_fmt(f), OPS.get(op, op), _ptr(a), _ptr(b), _ptr(c), _ptr(out), n)
+    return arr, len(specs)
+
+
+class BatchPlan:
+    """Owns a bsfp_batch_plan; the tensors the jobs point at must outlive it."""
+
+    def __init__(self, jobs, njobs: int, mode: int = BATCH_PERSISTENT, wpt: int = 0, blocks_per_sm: int = 0):
+        self._h = ctypes.c_void_p()
+        opt = bsfp_batch_options(mode, wpt, blocks_per_sm)
+        _check(_lib().bsfp_batch_plan_create(jobs, njobs, ctypes.byref(opt), ctypes.byref(self._h)),
+               "bsfp_batch_plan_create")
+
+    def run(self, stream=None):
+        _check(_lib().bsfp_batch_run(self._h, _stream(stream)), "bsfp_batch_run")
+
+    @property
+    def launches(self) -> int:
+        return int(_lib().bsfp_batch_launches(self._h))
+
+    def free(self):
+        if self._h:
+            _lib().bsfp_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def bsfp_batch_plan_create(jobs, njobs: int, mode: int = BATCH_PERSISTENT, wpt: int = 0,
+                           blocks_per_sm: int = 0) -> BatchPlan:
+    return BatchPlan(jobs, njobs, mode, wpt, blocks_per_sm)
+
+
+def bsfp_launch_jobs(jobs, njobs: int, stream=None):
+    _check(_lib().bsfp_launch_jobs(jobs, njobs, _stream(stream)), "bsfp_launch_jobs")
 
 
 # ------------------------------------------------------- bench support ---

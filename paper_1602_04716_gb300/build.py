@@ -44,7 +44,9 @@ def _units():
         units.append(("gatecount_e%d.o" % e,
                       ["g++", "-std=c++17", "-O1", "-fPIC", "-I", CSRC, "-DBSFP_E=%d" % e, "-c",
                        os.path.join(CSRC, "gatecount.cpp")]))
-    for src in ("api.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):
+    for opc in range(3):
+        units.append(("batch_opc%d.o" % opc, cu + ["-DBSFP_BATCH_OPC=%d" % opc, os.path.join(CSRC, "batch_inst.cu")]))
+    for src in ("api.cu", "batch.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):
         units.append((src.replace(".cu", ".o"), cu + [os.path.join(CSRC, src)]))
     return units
 
@@ -72,7 +74,7 @@ def build(jobs: int | None = None, verbose: bool = False) -> str:
         return o, None
 
     # longest units first
-    todo.sort(key=lambda t: (not t[0].startswith("binop"), t[0]))
+    todo.sort(key=lambda t: (not t[0].startswith(("binop", "batch_opc")), t[0]))
     errors = []
     with ThreadPoolExecutor(jobs) as ex:
         for o, err in ex.map(run, todo):

@@ -18,6 +18,7 @@
 
 #include "binop.cuh"
 #include "bsfp.h"
+#include "internal.h"
 
 namespace bsfp {
 
@@ -32,7 +33,6 @@ BSFP_DECL_REG(8)
 
 cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st);
 cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st);
-int device_num_sms();
 
 static std::once_flag g_init_once;
 static void init_tables() {
@@ -63,16 +63,16 @@ static bsfp_status cuda_fail(cudaError_t e) {
     return BSFP_ERR_CUDA;
 }
 
-static bool format_ok(const bsfp_format& f) {
+bool format_ok(const bsfp_format& f) {
     return f.exp_bits >= 2 && f.exp_bits <= 8 && f.man_bits >= 1 && f.man_bits <= 23 &&
            1 + f.exp_bits + f.man_bits <= 32 && (f.rnd == BSFP_RN || f.rnd == BSFP_RZ);
 }
 
 static int bits_of(const bsfp_format& f) { return 1 + f.exp_bits + f.man_bits; }
 
-static bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
-static int opclass(int op) {
+int opclass(int op) {
     switch (op) {
         case BSFP_OP_ADD:
         case BSFP_OP_SUB: return OPC_ADDSUB;
@@ -99,20 +99,26 @@ static int occupancy(const bsfp_format& f, int opc, const BinopEntry* e, int wpt
     return o;
 }
 
-/* Run one element-wise op. */
-static bsfp_status run_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
-                             uint32_t* out, int64_t n, cudaStream_t s) {
+/* Validate one element-wise op and work out its launch: kernel entry, args,
+ * words per thread and grid.  Returns BSFP_OK with *skip set when n == 0. */
+bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                          uint32_t* out, int64_t n, PreparedOp* po) {
+    po->skip = false;
     if (!format_ok(f)) return BSFP_ERR_FORMAT;
-    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
-    if (n == 0) return BSFP_OK;
     const int opc = opclass(op);
+    if (opc < 0) return BSFP_ERR_UNSUPPORTED;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) {
+        po->skip = true;
+        return BSFP_OK;
+    }
     if (!a || !b || !out || (opc == OPC_FMA2 && !c)) return BSFP_ERR_NULL;
     if (!aligned(a, 16) || !aligned(b, 16) || !aligned(out, 16) || (opc == OPC_FMA2 && !aligned(c, 16)))
         return BSFP_ERR_ALIGN;
     const BinopEntry* e = entry_for(f, opc);
     if (!e) return BSFP_ERR_UNSUPPORTED;
 
-    BinopArgs p;
+    BinopArgs& p = po->args;
     p.a = a;
     p.b = b;
     p.c = c;
@@ -121,6 +127,8 @@ static bsfp_status run_binop(const bsfp_format& f, int op, const uint32_t* a, co
     p.nwords = (n + 31) / 32;
     p.tailmask = (n % 32) ? ((1u << (n % 32)) - 1u) : ~0u;
     p.negb = (op == BSFP_OP_SUB) ? ~0u : 0u;
+    po->entry = e;
+    po->opc = opc;
 
     int wpt, bps;
     {
@@ -133,11 +141,31 @@ static bsfp_status run_binop(const bsfp_format& f, int op, const uint32_t* a, co
     const int64_t chunks = p.S / wpt;
     const int64_t need = (chunks + 127) / 128;
     const int64_t cap = (int64_t)device_num_sms() * bps;
-    const int grid = (int)(need < cap ? need : cap);
-    const cudaError_t err = e->launch(p, wpt, grid, s);
-    if (err != cudaSuccess) return cuda_fail(err);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    po->wpt = wpt;
+    po->grid = (int)(need < cap ? need : cap);
     return BSFP_OK;
+}
+
+bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s) {
+    if (po.skip) return BSFP_OK;
+    const cudaError_t err = po.entry->launch(po.args, po.wpt, po.grid, s);
+    if (err != cudaSuccess) return cuda_fail(err);
+    return BSFP_OK;
+}
+
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+bsfp_status set_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+/* Run one element-wise op. */
+static bsfp_status run_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                             uint32_t* out, int64_t n, cudaStream_t s) {
+    PreparedOp po;
+    const bsfp_status st = prepare_binop(f, op, a, b, c, out, n, &po);
+    if (st != BSFP_OK || po.skip) return st;
+    const bsfp_status r = launch_prepared(po, s);
+    if (r == BSFP_OK) count_launches(1);
+    return r;
 }
 
 }  // namespace bsfp

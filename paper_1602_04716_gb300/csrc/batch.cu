@@ -1,0 +1,239 @@
+/*
+ * batch.cu -- host side of the batched launch (bsfp.h): plan building,
+ * CUDA-graph capture, runs, and the per-job plain-launch comparator.
+ */
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "batch.cuh"
+#include "bsfp.h"
+#include "internal.h"
+
+namespace bsfp {
+
+batch_launch_fn batch_launcher_opc0(int wpt);
+batch_launch_fn batch_launcher_opc1(int wpt);
+batch_launch_fn batch_launcher_opc2(int wpt);
+const void* batch_kernel_ptr_opc0(int wpt);
+const void* batch_kernel_ptr_opc1(int wpt);
+const void* batch_kernel_ptr_opc2(int wpt);
+
+batch_launch_fn batch_launcher(int opc, int wpt) {
+    switch (opc) {
+        case OPC_ADDSUB: return batch_launcher_opc0(wpt);
+        case OPC_MUL: return batch_launcher_opc1(wpt);
+        case OPC_FMA2: return batch_launcher_opc2(wpt);
+    }
+    return nullptr;
+}
+
+const void* batch_kernel_ptr(int opc, int wpt) {
+    switch (opc) {
+        case OPC_ADDSUB: return batch_kernel_ptr_opc0(wpt);
+        case OPC_MUL: return batch_kernel_ptr_opc1(wpt);
+        case OPC_FMA2: return batch_kernel_ptr_opc2(wpt);
+    }
+    return nullptr;
+}
+
+}  // namespace bsfp
+
+using namespace bsfp;
+
+struct bsfp_batch_plan_st {
+    void* dev = nullptr;           /* descriptors | tile maps | counters */
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+};
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static void plan_destroy(bsfp_batch_plan p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->dev) cudaFree(p->dev);
+    delete p;
+}
+
+extern "C" {
+
+bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bsfp_batch_options* opt,
+                                   bsfp_batch_plan* plan_out) {
+    if (!plan_out) return BSFP_ERR_NULL;
+    *plan_out = nullptr;
+    if (njobs < 0) return BSFP_ERR_SIZE;
+    if (njobs > 0 && !jobs) return BSFP_ERR_NULL;
+    bsfp_batch_options o = {BSFP_BATCH_PERSISTENT, 2, 0};
+    if (opt) o = *opt;
+    if (o.wpt == 0) o.wpt = 2;
+    if ((o.mode != BSFP_BATCH_PERSISTENT && o.mode != BSFP_BATCH_PLAIN) || (o.wpt != 1 && o.wpt != 2) ||
+        o.blocks_per_sm < 0 || o.blocks_per_sm > 64)
+        return BSFP_ERR_SIZE;
+
+    /* validate every job and sort it into a persistent group or the plain list */
+    std::vector<PreparedOp> prep((size_t)njobs);
+    std::vector<int> group((size_t)njobs, -1);
+    for (int32_t i = 0; i < njobs; ++i) {
+        const bsfp_job& j = jobs[i];
+        const bsfp_status st = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &prep[(size_t)i]);
+        if (st != BSFP_OK) return st;
+        if (o.mode == BSFP_BATCH_PERSISTENT && !prep[(size_t)i].skip &&
+            batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0)
+            group[(size_t)i] = prep[(size_t)i].opc;
+    }
+
+    /* tiles per group */
+    const int64_t TILE = 128LL * o.wpt * BATCH_ROUNDS;
+    std::vector<JobDesc> desc[OPC_COUNT];
+    std::vector<int32_t> tmap[OPC_COUNT];
+    for (int32_t i = 0; i < njobs; ++i) {
+        const int g = group[(size_t)i];
+        if (g < 0) continue;
+        const bsfp_job& j = jobs[i];
+        const BinopArgs& a = prep[(size_t)i].args;
+        JobDesc d;
+        memset(&d, 0, sizeof d);
+        d.a = a.a;
+        d.b = a.b;
+        d.c = a.c;
+        d.out = a.out;
+        d.S = a.S;
+        d.nwords = a.nwords;
+        d.tile0 = (int64_t)tmap[g].size();
+        d.tailmask = a.tailmask;
+        d.negb = a.negb;
+        d.kind = batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd);
+        const int64_t nt = (a.S + TILE - 1) / TILE;
+        const int32_t idx = (int32_t)desc[g].size();
+        desc[g].push_back(d);
+        for (int64_t t = 0; t < nt; ++t) tmap[g].push_back(idx);
+    }
+
+    /* one device buffer: descriptors, tile maps, counters */
+    size_t off_desc[OPC_COUNT], off_map[OPC_COUNT], off_cnt[OPC_COUNT], total = 0;
+    for (int g = 0; g < OPC_COUNT; ++g) {
+        off_desc[g] = total;
+        total = align_up(total + desc[g].size() * sizeof(JobDesc), 256);
+        off_map[g] = total;
+        total = align_up(total + tmap[g].size() * sizeof(int32_t), 256);
+        off_cnt[g] = total;
+        total = align_up(total + sizeof(unsigned long long), 256);
+    }
+
+    bsfp_batch_plan p = new bsfp_batch_plan_st();
+    cudaError_t err = cudaMalloc(&p->dev, total);
+    if (err != cudaSuccess) {
+        plan_destroy(p);
+        return set_cuda_error(err);
+    }
+    char* base = static_cast<char*>(p->dev);
+    for (int g = 0; g < OPC_COUNT && err == cudaSuccess; ++g) {
+        if (!desc[g].empty()) err = cudaMemcpy(base + off_desc[g], desc[g].data(), desc[g].size() * sizeof(JobDesc),
+                                               cudaMemcpyHostToDevice);
+        if (err == cudaSuccess && !tmap[g].empty())
+            err = cudaMemcpy(base + off_map[g], tmap[g].data(), tmap[g].size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice);
+    }
+    if (err != cudaSuccess) {
+        plan_destroy(p);
+        return set_cuda_error(err);
+    }
+
+    /* capture: per group, clear the counter and run the persistent kernel;
+     * then the plain launches */
+    /* persistent grids: resident CTAs per SM x SMs, at most one CTA per tile */
+    int grid[OPC_COUNT] = {0, 0, 0};
+    for (int g = 0; g < OPC_COUNT; ++g) {
+        if (tmap[g].empty()) continue;
+        int occ = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(g, o.wpt), 128, 0);
+        if (err != cudaSuccess) {
+            plan_destroy(p);
+            return set_cuda_error(err);
+        }
+        if (occ < 1) occ = 1;
+        const int bps = (o.blocks_per_sm > 0 && o.blocks_per_sm < occ) ? o.blocks_per_sm : occ;
+        const int64_t ntiles = (int64_t)tmap[g].size();
+        const int64_t cap = (int64_t)device_num_sms() * bps;
+        grid[g] = (int)(ntiles < cap ? ntiles : cap);
+    }
+
+    cudaStream_t cs;
+    err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (err != cudaSuccess) {
+        plan_destroy(p);
+        return set_cuda_error(err);
+    }
+    bsfp_status st = BSFP_OK;
+    err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        for (int g = 0; g < OPC_COUNT && st == BSFP_OK; ++g) {
+            if (tmap[g].empty()) continue;
+            unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + off_cnt[g]);
+            cudaError_t e2 = cudaMemsetAsync(cnt, 0, sizeof *cnt, cs);
+            if (e2 == cudaSuccess)
+                e2 = batch_launcher(g, o.wpt)(reinterpret_cast<const JobDesc*>(base + off_desc[g]),
+                                              reinterpret_cast<const int32_t*>(base + off_map[g]),
+                                              (int64_t)tmap[g].size(), cnt, grid[g], cs);
+            if (e2 != cudaSuccess) st = set_cuda_error(e2);
+            else p->launches += 1;
+        }
+        for (int32_t i = 0; i < njobs && st == BSFP_OK; ++i) {
+            if (group[(size_t)i] >= 0 || prep[(size_t)i].skip) continue;
+            st = launch_prepared(prep[(size_t)i], cs);
+            if (st == BSFP_OK) p->launches += 1;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e3 = cudaStreamEndCapture(cs, &g);
+        p->graph = g;
+        if (st == BSFP_OK && e3 != cudaSuccess) st = set_cuda_error(e3);
+    } else {
+        st = set_cuda_error(err);
+    }
+    cudaStreamDestroy(cs);
+    if (st == BSFP_OK) {
+        err = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        if (err != cudaSuccess) st = set_cuda_error(err);
+    }
+    if (st != BSFP_OK) {
+        plan_destroy(p);
+        return st;
+    }
+    *plan_out = p;
+    return BSFP_OK;
+}
+
+bsfp_status bsfp_batch_run(bsfp_batch_plan plan, bsfp_stream_t s) {
+    if (!plan) return BSFP_ERR_NULL;
+    const cudaError_t err = cudaGraphLaunch(plan->exec, (cudaStream_t)s);
+    if (err != cudaSuccess) return set_cuda_error(err);
+    count_launches(plan->launches);
+    return BSFP_OK;
+}
+
+int64_t bsfp_batch_launches(bsfp_batch_plan plan) { return plan ? plan->launches : -1; }
+
+void bsfp_batch_free(bsfp_batch_plan plan) { plan_destroy(plan); }
+
+bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s) {
+    if (njobs < 0) return BSFP_ERR_SIZE;
+    if (njobs > 0 && !jobs) return BSFP_ERR_NULL;
+    for (int32_t i = 0; i < njobs; ++i) {
+        PreparedOp po;
+        const bsfp_job& j = jobs[i];
+        bsfp_status st = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &po);
+        if (st == BSFP_OK && !po.skip) {
+            st = launch_prepared(po, (cudaStream_t)s);
+            if (st == BSFP_OK) count_launches(1);
+        }
+        if (st != BSFP_OK) return st;
+    }
+    return BSFP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+/*
+ * internal.h -- declarations shared by the library's host-side translation
+ * units (not part of the public ABI).
+ */
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "binop.cuh"
+#include "bsfp.h"
+
+namespace bsfp {
+
+/* A validated element-wise op, ready to launch. */
+struct PreparedOp {
+    BinopArgs args;
+    const BinopEntry* entry;
+    int opc;
+    int wpt;
+    int grid;
+    bool skip;   /* n == 0: nothing to launch */
+};
+
+bool format_ok(const bsfp_format& f);
+bool aligned(const void* p, uintptr_t a);
+int opclass(int op);
+int device_num_sms();
+bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                          uint32_t* out, int64_t n, PreparedOp* po);
+bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s);
+void count_launches(int64_t k);
+bsfp_status set_cuda_error(cudaError_t e);
+
+}  // namespace bsfp

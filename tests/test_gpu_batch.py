@@ -1,0 +1,134 @@
+"""The batched launch: every job of a mixed batch (formats, ops, roundings,
+lengths from 0 to tens of thousands, plus formats outside the persistent set)
+is bit-identical to the oracle and to the same job run alone, in the
+persistent plan, in the graph of plain launches and as plain launches without
+a graph; graph replays give the same result again."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_1602_04716_gb300 as bs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+OPS = ["add", "sub", "mul", "fma2"]
+
+
+def _dev(x: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(x).view(np.int32).copy()).cuda()
+
+
+def _make_batch(njobs, seed, max_len=1 << 16, extra_formats=((6, 9), (3, 2), (8, 23))):
+    r = synth.splitmix64(seed, 4 * njobs)
+    fmts = bs.BATCH_FORMATS + list(extra_formats)
+    lens = synth.log_uniform_lengths(njobs, 1, max_len, seed, 1)
+    jobs = []
+    for i in range(njobs):
+        E, M = fmts[int(r[4 * i] % len(fmts))]
+        op = OPS[int(r[4 * i + 1] % 4)]
+        rnd = int(r[4 * i + 2] % 2)
+        n = int(lens[i]) if i % 17 else (0 if i % 34 == 0 else int(lens[i]) + 31)
+        B = 1 + E + M
+        a, b, c = (synth.fp_values(E, M, n, seed + 10 * i + k).astype(np.uint32) for k in (1, 2, 3))
+        t = {k: _dev(oracle.pack(B, v)) for k, v in (("a", a), ("b", b), ("c", c))}
+        t["out"] = torch.full_like(t["a"], -1)
+        jobs.append(dict(E=E, M=M, op=op, rnd=rnd, n=n, a=a, b=b, c=c, t=t))
+    return jobs
+
+
+def _ctypes_jobs(jobs):
+    return bs.make_jobs((bs.Format(j["E"], j["M"], j["rnd"]), j["op"], j["t"]["a"], j["t"]["b"],
+                         j["t"]["c"] if j["op"] == "fma2" else None, j["t"]["out"], j["n"]) for j in jobs)
+
+
+def _check_all(jobs):
+    for i, j in enumerate(jobs):
+        B = 1 + j["E"] + j["M"]
+        want = oracle.pack(B, oracle.binop(j["op"], j["E"], j["M"], j["rnd"], j["a"], j["b"], j["c"]))
+        got = j["t"]["out"].cpu().numpy().view(np.uint32).reshape(B, -1)
+        if j["n"] == 0:
+            continue
+        assert (got == want).all(), "job %d: %s 1/%d/%d rnd=%d n=%d" % (i, j["op"], j["E"], j["M"], j["rnd"], j["n"])
+
+
+def _clear(jobs):
+    for j in jobs:
+        j["t"]["out"].fill_(-1)
+
+
+@pytest.mark.parametrize("wpt", [1, 2])
+def test_persistent_plan_matches_oracle_and_replays(wpt):
+    jobs = _make_batch(220, 5000 + wpt)
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_PERSISTENT, wpt)
+    n_plain = sum(1 for j in jobs if (j["E"], j["M"]) not in bs.BATCH_FORMATS and j["n"] > 0)
+    assert plan.launches >= n_plain + 1
+    for _ in range(2):   # the second run replays the graph with the counters cleared again
+        _clear(jobs)
+        plan.run()
+        torch.cuda.synchronize()
+        _check_all(jobs)
+    plan.free()
+
+
+@pytest.mark.parametrize("blocks_per_sm", [1, 2])
+def test_persistent_plan_small_grids(blocks_per_sm):
+    """Few resident CTAs: every CTA loops over many tiles."""
+    jobs = _make_batch(60, 7100 + blocks_per_sm, max_len=1 << 18, extra_formats=())
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_PERSISTENT, 2, blocks_per_sm)
+    plan.run()
+    torch.cuda.synchronize()
+    _check_all(jobs)
+    plan.free()
+
+
+def test_plain_graph_and_plain_launches_match():
+    jobs = _make_batch(120, 8000)
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_PLAIN)
+    assert plan.launches == sum(1 for j in jobs if j["n"] > 0)
+    plan.run()
+    torch.cuda.synchronize()
+    _check_all(jobs)
+    plan.free()
+    _clear(jobs)
+    before = bs.bsfp_launch_count()
+    bs.bsfp_launch_jobs(arr, nj)
+    torch.cuda.synchronize()
+    assert bs.bsfp_launch_count() - before == sum(1 for j in jobs if j["n"] > 0)
+    _check_all(jobs)
+
+
+def test_each_job_alone_equals_the_mix():
+    jobs = _make_batch(40, 9000)
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj)
+    plan.run()
+    torch.cuda.synchronize()
+    mixed = [j["t"]["out"].clone() for j in jobs]
+    plan.free()
+    for j, m in zip(jobs, mixed):
+        j["t"]["out"].fill_(-1)
+        bs.bsfp_op(j["op"], bs.Format(j["E"], j["M"], j["rnd"]), j["t"]["a"], j["t"]["b"], j["t"]["out"], j["n"],
+                   c=j["t"]["c"])
+        torch.cuda.synchronize()
+        if j["n"]:
+            assert torch.equal(j["t"]["out"], m)
+
+
+def test_invalid_job_rejected_before_anything_runs():
+    jobs = _make_batch(5, 9100, extra_formats=())
+    arr, nj = _ctypes_jobs(jobs)
+    arr[3].f.exp_bits = 9
+    with pytest.raises(bs.BsfpError) as ei:
+        bs.BatchPlan(arr, nj)
+    assert ei.value.status == bs.ERR_FORMAT
+    arr[3].f.exp_bits = 4
+    arr[2].a = arr[2].a + 4 if arr[2].a else 4
+    with pytest.raises(bs.BsfpError) as ei:
+        bs.BatchPlan(arr, nj)
+    assert ei.value.status in (bs.ERR_ALIGN, bs.ERR_NULL)
