@@ -37,9 +37,11 @@
 
 #if defined(__CUDACC__)
 #define BSFP_HD __host__ __device__ __forceinline__
+#define BSFP_HDC __host__ __device__
 #define BSFP_UNROLL _Pragma("unroll")
 #else
 #define BSFP_HD inline
+#define BSFP_HDC
 #define BSFP_UNROLL _Pragma("GCC unroll 128")
 #endif
 
@@ -130,7 +132,7 @@ template <int N, int ND, int K = 0, class W> BSFP_HD void rshift_sticky(W* x, co
     }
 }
 
-constexpr int floor_log2(int v) { return v <= 1 ? 0 : 1 + floor_log2(v / 2); }
+BSFP_HDC constexpr int floor_log2(int v) { return v <= 1 ? 0 : 1 + floor_log2(v / 2); }
 
 /* One stage of the normalising left shifter: shift by S = 2^K when the top S
  * bits of z are zero and the remaining budget allows it.  The budget test is
