@@ -167,6 +167,41 @@ void bsfp_batch_free(bsfp_batch_plan plan);
  * already queued). */
 bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s);
 
+/* Limits of bsfp_batch_run_noalloc: jobs per call, and tiles per call (one
+ * tile = 32,768 elements of one job, rounded up per job, counting only jobs in
+ * the persistent formats).  Its fixed scratch is sized from these: about
+ * 1.5 MB of device memory per GPU that loads the library. */
+#define BSFP_NOALLOC_MAX_JOBS 4096
+#define BSFP_NOALLOC_MAX_TILES (1 << 18)
+
+/* The batched launch without any allocation.  The paper has no counterpart;
+ * this serves callers that must not allocate device memory themselves: an
+ * application whose own pool has reserved the device memory up front, so a
+ * cudaMalloc from a library fails or takes memory it has budgeted, and
+ * latency-bound loops, where cudaMalloc/cudaFree can synchronise the whole
+ * device.  The jobs run exactly as in a persistent plan (same kernels, same
+ * results), launched directly on s; jobs outside the persistent formats run as
+ * their plain kernels.
+ *
+ * The scratch a plan would allocate (job descriptors, tile map, counters)
+ * lives instead in one fixed array in device memory that every GPU loading
+ * the library holds until the process exits; no call allocates or frees
+ * anything, on the host or the device.  Every call shares that array and
+ * leaves its contents behind; each call rebuilds what it reads and zeroes its
+ * counters.  Calls on one stream run one after another; calls that overlap
+ * on the GPU (other streams, other host threads) race on the array and give
+ * wrong results.  The first call on a device also looks up the array's device
+ * address and the kernels' occupancy; make that first call before any stream
+ * capture.
+ *
+ * jobs is host memory read by an asynchronous copy on s: pageable memory is
+ * staged before the call returns; page-locked memory must stay unchanged
+ * until s has passed the call.  Errors: njobs < 0 or > BSFP_NOALLOC_MAX_JOBS,
+ * or more than BSFP_NOALLOC_MAX_TILES tiles, return BSFP_ERR_SIZE; any
+ * invalid job returns its bsfp_add/... error.  All checks come before
+ * anything is launched. */
+bsfp_status bsfp_batch_run_noalloc(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s);
+
 /* ---------------------------------------------------------- diagnostics --- */
 const char* bsfp_status_str(int32_t status);
 /* The cudaError_t of the last BSFP_ERR_CUDA on this thread (0 if none). */

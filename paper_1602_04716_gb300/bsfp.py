@@ -107,6 +107,7 @@ def _lib():
                 "bsfp_batch_launches": (i64, [p]),
                 "bsfp_batch_free": (None, [p]),
                 "bsfp_launch_jobs": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
+                "bsfp_batch_run_noalloc": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -273,6 +274,15 @@ def bsfp_batch_plan_create(jobs, njobs: int, mode: int = BATCH_PERSISTENT, wpt: 
 
 def bsfp_launch_jobs(jobs, njobs: int, stream=None):
     _check(_lib().bsfp_launch_jobs(jobs, njobs, _stream(stream)), "bsfp_launch_jobs")
+
+
+NOALLOC_MAX_JOBS, NOALLOC_MAX_TILES = 4096, 1 << 18
+
+
+def bsfp_batch_run_noalloc(jobs, njobs: int, stream=None):
+    """The batched launch with its scratch in the library's fixed device array
+    (no allocation); for callers that must not allocate device memory."""
+    _check(_lib().bsfp_batch_run_noalloc(jobs, njobs, _stream(stream)), "bsfp_batch_run_noalloc")
 
 
 # ------------------------------------------------------- bench support ---
