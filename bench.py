@@ -310,6 +310,10 @@ def run_gpu(args):
     if args.batch_jobs > 0:
         batched = run_batched(bs, torch, args, rank, hbm)
 
+    serving = None
+    if args.serve_seconds > 0:
+        serving = run_serving(bs, torch, args, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -324,7 +328,7 @@ def run_gpu(args):
                            "seeds": [synth.SEED_A, synth.SEED_B], "parallelism": "dp%d" % world,
                            "tuned_shapes_applied": tuned},
                 "roofline": roof, "kernels": kinfo, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-                "cpu_baseline": cpu, "batched": batched}
+                "cpu_baseline": cpu, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -407,6 +411,56 @@ def run_batched(bs, torch, args, rank, hbm):
     return res
 
 
+def run_serving(bs, torch, args, rank):
+    """Serving loop: Poisson arrivals of bs_add/bs_mul requests (lengths
+    log-uniform in [256, 2^22], formats uniform over the batched set, RN) on
+    device-resident operands, results from a 64 GB budget, through the
+    library's server (continuous batching); open-loop replay in native code."""
+    pool = args.serve_pool
+    arr, nj, keep, _, _ = batched_workload(bs, torch, pool, 256, 1 << 22, 19700101, rank)
+    src = [arr[i] for i in range(nj)]
+    out = {}
+    for name, rate, nreq in (("poisson", args.serve_rate, int(args.serve_rate * args.serve_seconds)),
+                             ("saturated", None, args.serve_saturated)):
+        pick = synth.splitmix64(424242 + int(rate or 0), nreq, 2 * rank)
+        jobs = (bs.bsfp_job * nreq)()
+        elems = 0
+        for i in range(nreq):
+            j = src[int(pick[i] % nj)]
+            jobs[i] = bs.bsfp_job(j.f, j.op, j.a, j.b, j.c, None, j.n)
+            elems += j.n
+        if rate:
+            gaps = -np.log1p(-synth.uniform01(nreq, 8675309, 2 * rank)) / rate
+            arrival = np.cumsum(gaps * 1e9).astype(np.int64)
+        else:
+            arrival = np.zeros(nreq, dtype=np.int64)
+        srv = bs.Server(64 << 30, slots=args.serve_slots)
+        # warm-up: a short slice of the same trace
+        w = min(nreq, 256)
+        srv.replay(jobs, w, arrival[:w] - arrival[0], release=True)
+        done = srv.replay(jobs, nreq, arrival, release=True, timeout_ms=120000)
+        st = srv.stats()
+        srv.close()
+        sub = np.array([done[i].t_submit_ns for i in range(nreq)], dtype=np.int64)
+        fin = np.array([done[i].t_done_ns for i in range(nreq)], dtype=np.int64)
+        lat_us = (fin - sub) / 1e3
+        span = (fin.max() - sub.min()) / 1e9
+        out[name] = {"requests": nreq, "offered_requests_per_s": rate,
+                     "achieved_requests_per_s": nreq / span, "elements_per_s": elems / span,
+                     "latency_us": {"p50": float(np.percentile(lat_us, 50)), "p99": float(np.percentile(lat_us, 99)),
+                                    "p999": float(np.percentile(lat_us, 99.9)), "max": float(lat_us.max())},
+                     "micro_batches": st["batches"],
+                     "peak_inflight_batches": st["peak_inflight_batches"],
+                     "arena_peak_bytes": st["arena_peak_bytes"], "failed": st["failed"]}
+    out["workload"] = ("Poisson arrivals at %g requests/s for %g s (and a saturated run of %d requests arriving "
+                       "at once); bs_add/bs_mul 50/50, RN; lengths log-uniform in [256, 4194304]; formats %s uniform; "
+                       "operands drawn from %d device-resident pairs; results from a 64 GB budget; %d slots"
+                       % (args.serve_rate, args.serve_seconds, args.serve_saturated,
+                          ["1/%d/%d" % fm for fm in BATCH_FORMATS], pool, args.serve_slots))
+    del keep
+    return out
+
+
 def run_e2e(bs, torch, n, rank, args):
     """Per step: pinned host standard arrays -> device -> pack -> add, mul ->
     unpack -> host, for both formats, all through the library's C ABI."""
@@ -483,6 +537,11 @@ def main(argv=None):
                     help="vectors in the batched comparison (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-wpt", type=int, default=0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="Poisson serving run length (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=20000.0, help="requests/s")
+    ap.add_argument("--serve-saturated", type=int, default=20000, help="requests in the saturated run")
+    ap.add_argument("--serve-pool", type=int, default=2048, help="device-resident operand pairs")
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -69,7 +69,7 @@ typedef enum {
     BSFP_ERR_SIZE = -4,        /* n < 0 or n > BSFP_MAX_N, or a bad count */
     BSFP_ERR_UNSUPPORTED = -5, /* valid request that this build does not cover */
     BSFP_ERR_CUDA = -6,        /* a CUDA call failed; see bsfp_last_cuda_error */
-    BSFP_ERR_BUDGET = -7,      /* reserved for admission control */
+    BSFP_ERR_BUDGET = -7,      /* a request larger than a server's whole budget */
     BSFP_ERR_TIMEOUT = -8      /* a bounded wait ran out */
 } bsfp_status;
 
@@ -201,6 +201,82 @@ bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t 
  * invalid job returns its bsfp_add/... error.  All checks come before
  * anything is launched. */
 bsfp_status bsfp_batch_run_noalloc(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s);
+
+/* -------------------------------------------------------------- serving --- */
+/* A request server for element-wise ops on device-resident bitslice operands
+ * (not part of the paper: a serving form of the Sec. 4 operations).  Requests
+ * of any compiled format, op and length are submitted from any host thread;
+ * a worker thread of the server admits them in arrival order while its
+ * result memory and its in-flight slots allow, groups everything admitted at
+ * once into a micro-batch and runs it as the persistent batched kernels on
+ * one of several streams, so micro-batches admitted while others are still
+ * on the GPU run alongside them (continuous batching).  Results stay on the
+ * device until released, so they can be operands of later requests.
+ *
+ * Memory.  The server allocates, at creation, one device arena of
+ * budget_bytes for results and small per-slot descriptor buffers; nothing is
+ * allocated per request.  A request whose out is NULL gets its result planes
+ * (bsfp_bitslice_bytes of its format and n, rounded up to 256 bytes; none
+ * when n == 0) from the arena at admission; a request is admitted only when that fits, strictly in
+ * arrival order (a request that does not fit waits, and so do those behind
+ * it).  A request with its own out uses no arena memory.  The operands are
+ * the caller's and must stay valid until the request completes. */
+typedef struct bsfp_server_st* bsfp_server;
+
+typedef struct {
+    int64_t budget_bytes;    /* result arena, bytes (> 0) */
+    int32_t slots;           /* micro-batches in flight at once, 1..16 (0 = 4) */
+    int32_t max_batch_jobs;  /* requests per micro-batch, 1..4096 (0 = 1024) */
+    int32_t max_batch_tiles; /* 32,768-element tiles per micro-batch, 128..2^20 (0 = 2^16) */
+    int32_t wpt;             /* words per thread of the persistent kernels, 1 or 2 (0 = 2) */
+} bsfp_server_options;
+
+/* One finished request.  Times are host steady-clock nanoseconds: submission,
+ * admission (its micro-batch launched) and completion (the worker saw the
+ * micro-batch's event complete). */
+typedef struct {
+    int64_t id;
+    int32_t status;      /* BSFP_OK, or the error that failed it */
+    int32_t pad;
+    uint32_t* out;       /* the result planes */
+    int64_t n;
+    int64_t t_submit_ns;
+    int64_t t_admit_ns;
+    int64_t t_done_ns;
+} bsfp_completion;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t pending;          /* submitted, not yet admitted */
+    int64_t inflight_batches; /* micro-batches on the GPU now */
+    int64_t batches;          /* micro-batches launched so far */
+    int64_t peak_inflight_batches;
+    int64_t arena_bytes_in_use, arena_peak_bytes, budget_bytes;
+    int64_t launches;         /* kernel launches so far */
+} bsfp_server_stats;
+
+/* Create a server on the current device (opt may be NULL only for defaults
+ * with a 1 GiB budget).  Errors: bad options BSFP_ERR_SIZE; allocation or
+ * stream creation failures BSFP_ERR_CUDA (nothing is left allocated). */
+bsfp_status bsfp_server_create(const bsfp_server_options* opt, bsfp_server* out);
+/* Submit one request.  job->out may be NULL (result from the arena).  The job
+ * is validated here (same errors as bsfp_add etc.); a result larger than the
+ * whole budget returns BSFP_ERR_BUDGET.  *id_out receives the request id
+ * (increasing from 1).  Thread-safe; never blocks on the GPU. */
+bsfp_status bsfp_server_submit(bsfp_server srv, const bsfp_job* job, int64_t* id_out);
+/* Move up to max finished requests into done[] (oldest first); returns how
+ * many.  Thread-safe. */
+int32_t bsfp_server_poll(bsfp_server srv, bsfp_completion* done, int32_t max);
+/* Give back a finished request's arena memory (its out is invalid after
+ * this).  BSFP_ERR_SIZE if id is not a finished, unreleased request. */
+bsfp_status bsfp_server_release(bsfp_server srv, int64_t id);
+/* Wait until nothing is pending or in flight, at most timeout_ms
+ * (BSFP_ERR_TIMEOUT when it runs out). */
+bsfp_status bsfp_server_drain(bsfp_server srv, int64_t timeout_ms);
+bsfp_status bsfp_server_get_stats(bsfp_server srv, bsfp_server_stats* st);
+/* Stop the worker after the in-flight work ends and free everything; pending
+ * requests are dropped, results become invalid. */
+void bsfp_server_destroy(bsfp_server srv);
 
 /* ---------------------------------------------------------- diagnostics --- */
 const char* bsfp_status_str(int32_t status);

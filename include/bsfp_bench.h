@@ -36,6 +36,16 @@ bsfp_status bsfp_synth_fp_values(bsfp_format f, int64_t n, uint64_t seed, uint64
 bsfp_status bsfp_lop3_probe(uint32_t* sink, int32_t grid, int32_t block, int32_t iters, uint32_t seed,
                             bsfp_stream_t s);
 
+/* Open-loop replay of a request trace through a server: request i (job i)
+ * is submitted at arrival_ns[i] nanoseconds after the start (non-decreasing;
+ * the calling thread waits for each arrival time, polling completions
+ * meanwhile), and done[i] receives its completion.  With release != 0 every
+ * arena result is released as soon as it completes.  Returns when all have
+ * completed, or BSFP_ERR_TIMEOUT after timeout_ms.  A job that fails
+ * validation stops the replay with its error. */
+bsfp_status bsfp_server_replay(bsfp_server srv, const bsfp_job* jobs, const int64_t* arrival_ns, int32_t n,
+                               int32_t release, bsfp_completion* done, int64_t timeout_ms);
+
 /* Number of streaming multiprocessors of the current device (0 on error). */
 int32_t bsfp_num_sms(void);
 

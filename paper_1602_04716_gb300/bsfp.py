@@ -62,6 +62,23 @@ class bsfp_batch_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("wpt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
+class bsfp_server_options(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("max_batch_jobs", ctypes.c_int32),
+                ("max_batch_tiles", ctypes.c_int32), ("wpt", ctypes.c_int32)]
+
+
+class bsfp_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("out", ctypes.c_void_p), ("n", ctypes.c_int64), ("t_submit_ns", ctypes.c_int64),
+                ("t_admit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
+class bsfp_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "submitted", "completed", "failed", "pending", "inflight_batches", "batches", "peak_inflight_batches",
+        "arena_bytes_in_use", "arena_peak_bytes", "budget_bytes", "launches")]
+
+
 BATCH_PERSISTENT, BATCH_PLAIN = 0, 1
 BATCH_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
 
@@ -108,6 +125,15 @@ def _lib():
                 "bsfp_batch_free": (None, [p]),
                 "bsfp_launch_jobs": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
                 "bsfp_batch_run_noalloc": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
+                "bsfp_server_create": (i32, [ctypes.POINTER(bsfp_server_options), ctypes.POINTER(p)]),
+                "bsfp_server_submit": (i32, [p, ctypes.POINTER(bsfp_job), ctypes.POINTER(i64)]),
+                "bsfp_server_poll": (i32, [p, ctypes.POINTER(bsfp_completion), i32]),
+                "bsfp_server_release": (i32, [p, i64]),
+                "bsfp_server_drain": (i32, [p, i64]),
+                "bsfp_server_get_stats": (i32, [p, ctypes.POINTER(bsfp_server_stats)]),
+                "bsfp_server_destroy": (None, [p]),
+                "bsfp_server_replay": (i32, [p, ctypes.POINTER(bsfp_job), ctypes.POINTER(i64), i32, i32,
+                                             ctypes.POINTER(bsfp_completion), i64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -283,6 +309,74 @@ def bsfp_batch_run_noalloc(jobs, njobs: int, stream=None):
     """The batched launch with its scratch in the library's fixed device array
     (no allocation); for callers that must not allocate device memory."""
     _check(_lib().bsfp_batch_run_noalloc(jobs, njobs, _stream(stream)), "bsfp_batch_run_noalloc")
+
+
+# -------------------------------------------------------------- serving ---
+class Server:
+    """Owns a bsfp_server (continuous batching of requests on device-resident
+    operands).  Operand tensors must outlive the requests that use them."""
+
+    def __init__(self, budget_bytes: int, slots: int = 0, max_batch_jobs: int = 0, max_batch_tiles: int = 0,
+                 wpt: int = 0):
+        self._h = ctypes.c_void_p()
+        opt = bsfp_server_options(budget_bytes, slots, max_batch_jobs, max_batch_tiles, wpt)
+        _check(_lib().bsfp_server_create(ctypes.byref(opt), ctypes.byref(self._h)), "bsfp_server_create")
+
+    def submit(self, f, op, a, b, n: int, c=None, out=None) -> int:
+        job = bsfp_job(_fmt(f), OPS.get(op, op), _ptr(a), _ptr(b), _ptr(c), _ptr(out), n)
+        rid = ctypes.c_int64()
+        _check(_lib().bsfp_server_submit(self._h, ctypes.byref(job), ctypes.byref(rid)), "bsfp_server_submit")
+        return rid.value
+
+    def poll(self, max_items: int = 256) -> list:
+        buf = (bsfp_completion * max_items)()
+        k = _lib().bsfp_server_poll(self._h, buf, max_items)
+        return [buf[i] for i in range(k)]
+
+    def release(self, rid: int):
+        _check(_lib().bsfp_server_release(self._h, rid), "bsfp_server_release")
+
+    def drain(self, timeout_ms: int = 10000):
+        _check(_lib().bsfp_server_drain(self._h, timeout_ms), "bsfp_server_drain")
+
+    def stats(self) -> dict:
+        st = bsfp_server_stats()
+        _check(_lib().bsfp_server_get_stats(self._h, ctypes.byref(st)), "bsfp_server_get_stats")
+        return {k: getattr(st, k) for k, _ in bsfp_server_stats._fields_}
+
+    def replay(self, jobs, njobs: int, arrival_ns, release: bool = True, timeout_ms: int = 60000):
+        """Open-loop replay; arrival_ns: int64 numpy array.  Returns the
+        ctypes array of completions, one per job in submission order."""
+        import numpy as np
+        arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        done = (bsfp_completion * max(1, njobs))()
+        _check(_lib().bsfp_server_replay(self._h, jobs, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), njobs,
+                                         1 if release else 0, done, timeout_ms), "bsfp_server_replay")
+        return done
+
+    @staticmethod
+    def result(c: "bsfp_completion", f):
+        """The result planes of a finished request as an int32 device tensor
+        (a view of server memory: valid until the request is released)."""
+        import torch
+        words = _fmt(f).bits * bsfp_plane_stride(c.n)
+        if words == 0:
+            return torch.empty(0, dtype=torch.int32, device="cuda")
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (words,), "typestr": "<i4", "data": (c.out, False), "version": 3}
+        return torch.as_tensor(_View(), device="cuda")
+
+    def close(self):
+        if self._h:
+            _lib().bsfp_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------- bench support ---

@@ -120,3 +120,28 @@ def test_gate_counts_follow_table1_classes():
     for e, m in [(4, 3), (5, 10), (8, 23)]:
         for op in ("add", "mul"):
             assert g(e, m, op, 1) <= g(e, m, op, 0)
+
+
+def test_server_options_validated_before_any_cuda_call():
+    L = _binding._lib()
+    h = ctypes.c_void_p()
+    for bad in [(0, 4, 1024, 1 << 16, 2), (1 << 20, 17, 0, 0, 0), (1 << 20, 0, 5000, 0, 0),
+                (1 << 20, 0, 0, 64, 0), (1 << 20, 0, 0, 0, 3), (-1, 0, 0, 0, 0)]:
+        opt = _binding.bsfp_server_options(*bad)
+        assert L.bsfp_server_create(ctypes.byref(opt), ctypes.byref(h)) == bs.ERR_SIZE
+        assert not h.value
+    assert L.bsfp_server_create(None, None) == bs.ERR_NULL
+    rid = ctypes.c_int64()
+    assert L.bsfp_server_submit(None, None, ctypes.byref(rid)) == bs.ERR_NULL
+    assert L.bsfp_server_poll(None, None, 4) == 0
+    assert L.bsfp_server_release(None, 1) == bs.ERR_NULL
+    assert L.bsfp_server_drain(None, 1) == bs.ERR_NULL
+    L.bsfp_server_destroy(None)
+
+
+def test_noalloc_sizes_rejected_before_any_cuda_call():
+    L = _binding._lib()
+    jobs = (bs.bsfp_job * 1)()
+    assert L.bsfp_batch_run_noalloc(jobs, bs.NOALLOC_MAX_JOBS + 1, None) == bs.ERR_SIZE
+    assert L.bsfp_batch_run_noalloc(jobs, -1, None) == bs.ERR_SIZE
+    assert L.bsfp_batch_run_noalloc(jobs, 0, None) == bs.OK
