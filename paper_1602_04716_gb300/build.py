@@ -22,6 +22,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbsfp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+GEN_DIR = os.path.join(BUILD, "gen")
+GEN_HEADER = os.path.join(GEN_DIR, "gen_circuits.cuh")
+# Formats whose circuits are printed gate by gate from their netlists
+# (circuitgen): the formats of the benchmarks and of the batched kernels.
+GEN_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]
 
 
 def nvcc() -> str:
@@ -34,7 +39,8 @@ def nvcc() -> str:
 def _units():
     """(object name, compiler command without -o) for every translation unit."""
     nv = nvcc()
-    cu = [nv, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INC, "-c"]
+    cu = [nv, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INC, "-I", GEN_DIR,
+          "-DBSFP_HAVE_GEN", "-c"]
     units = []
     for e in range(2, 9):
         for lo, hi in ((1, 11), (12, 23)):
@@ -55,9 +61,27 @@ def _deps():
     return glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INC, "*.h"))
 
 
+def generate() -> str:
+    """Compile circuitgen for GEN_FORMATS and print their netlists into
+    _build/gen/gen_circuits.cuh (redone only when a circuit source changed)."""
+    os.makedirs(GEN_DIR, exist_ok=True)
+    srcs = [os.path.join(CSRC, f) for f in ("circuitgen.cpp", "netlist.h", "circuit.cuh")] + [__file__]
+    if os.path.exists(GEN_HEADER) and os.path.getmtime(GEN_HEADER) >= max(os.path.getmtime(p) for p in srcs):
+        return GEN_HEADER
+    tool = os.path.join(BUILD, "circuitgen")
+    fmts = " ".join("X(%d, %d)" % fm for fm in GEN_FORMATS)
+    subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", CSRC, "-DBSFP_GEN_FORMATS=" + fmts,
+                           os.path.join(CSRC, "circuitgen.cpp"), "-o", tool])
+    tmp = GEN_HEADER + ".tmp"
+    subprocess.check_call([tool, tmp])
+    os.replace(tmp, GEN_HEADER)
+    return GEN_HEADER
+
+
 def build(jobs: int | None = None, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(p) for p in _deps())
+    generate()
+    newest = max(os.path.getmtime(p) for p in _deps() + [GEN_HEADER])
     units = _units()
     todo = [(o, c) for o, c in units
             if not os.path.exists(os.path.join(BUILD, o)) or os.path.getmtime(os.path.join(BUILD, o)) < newest]

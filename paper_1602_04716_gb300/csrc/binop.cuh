@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include "circuit.cuh"
+#include "gen_circuit.cuh"
 
 namespace bsfp {
 
@@ -71,11 +72,15 @@ __device__ __forceinline__ void vstore(uint32_t* p, const uint32_t* w) {
 }
 
 /* The circuit for one word column.  OPC_ADDSUB takes the sign flip at run
- * time (one extra gate) so that add and sub share a kernel. */
+ * time (one extra gate) so that add and sub share a kernel.  Formats with a
+ * generated netlist (gen_circuit.cuh) run it; the others the templates. */
 template <int E, int M, bool RZ, int OPC>
 __device__ __forceinline__ void column_op(uint32_t* x, uint32_t* y, const uint32_t* z, uint32_t* r, uint32_t negb) {
     constexpr int B = 1 + E + M;
-    if constexpr (OPC == OPC_ADDSUB) {
+    if constexpr (GenCircuit<E, M, RZ, OPC>::available) {
+        if constexpr (OPC == OPC_ADDSUB) y[B - 1] ^= negb;
+        GenCircuit<E, M, RZ, OPC>::eval(x, y, z, r);
+    } else if constexpr (OPC == OPC_ADDSUB) {
         y[B - 1] ^= negb;
         fp_add<E, M, RZ, false>(x, y, r);
     } else if constexpr (OPC == OPC_MUL) {

@@ -1,8 +1,10 @@
-"""The library's circuit templates (circuit.cuh) evaluated on the host with
-32-bit words, compared bit for bit with the oracle.  This exercises the same
-gate-level code the CUDA kernels run, without a GPU: exhaustively over every
-operand pair for formats of at most 8 bits and on seeded samples for wider
-formats, for add, sub, mul and fma2 under RN and RZ."""
+"""The library's circuit templates (circuit.cuh), and the gate-by-gate
+netlists printed from them for the generated formats (gen_circuits.cuh),
+evaluated on the host with 32-bit words and compared bit for bit with the
+oracle.  This exercises the same gate-level code the CUDA kernels run,
+without a GPU: exhaustively over every operand pair for formats of at most 8
+bits and on seeded samples for wider formats, for add, sub, mul and fma2
+under RN and RZ."""
 import ctypes
 import os
 import subprocess
@@ -34,8 +36,28 @@ def _lib():
     return _L
 
 
-def circuit(E, M, rnd, op, a, b, c=None):
-    """Pack with the oracle's bit loop, run the circuit, unpack."""
+_G = None
+
+
+def _gen_lib():
+    """The generated netlists compiled for the host (the build prints them)."""
+    global _G
+    if _G is None:
+        from paper_1602_04716_gb300 import build
+        build.generate()
+        out = os.path.join(tempfile.gettempdir(), "bsfp_gen_circuit_host_%d.so" % os.getpid())
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-DBSFP_HAVE_GEN", "-I", CSRC,
+                               "-I", build.GEN_DIR, "-o", out, os.path.join(HERE, "gen_circuit_host.cpp")])
+        L = ctypes.CDLL(out)
+        L.host_gen_circuit.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 4 + [ctypes.c_long] * 2
+        L.host_gen_circuit.restype = ctypes.c_int
+        _G = L
+    return _G
+
+
+def circuit(E, M, rnd, op, a, b, c=None, generated=False):
+    """Pack with the oracle's bit loop, run the circuit (the template, or the
+    generated netlist), unpack."""
     B = 1 + E + M
     a = np.asarray(a, np.uint32)
     b = np.asarray(b, np.uint32)
@@ -43,8 +65,8 @@ def circuit(E, M, rnd, op, a, b, c=None):
     pa, pb, pc = oracle.pack(B, a), oracle.pack(B, b), oracle.pack(B, c)
     S = pa.shape[1]
     out = np.zeros_like(pa)
-    rc = _lib().host_circuit(E, M, rnd, OPS.index(op), pa.ctypes.data, pb.ctypes.data, pc.ctypes.data,
-                             out.ctypes.data, S, S)
+    fn = _gen_lib().host_gen_circuit if generated else _lib().host_circuit
+    rc = fn(E, M, rnd, OPS.index(op), pa.ctypes.data, pb.ctypes.data, pc.ctypes.data, out.ctypes.data, S, S)
     assert rc == 0, "format not in the host harness"
     return oracle.unpack(B, out, a.size)
 
@@ -99,5 +121,39 @@ def test_circuit_wide_sampled(E, M, rnd):
             a, b, c = (synth.uniform_bits(B, n, s).astype(np.uint32) for s in (31, 32, 33))
         for op in OPS:
             got = circuit(E, M, rnd, op, a, b, c)
+            want = oracle.binop(op, E, M, rnd, a, b, c)
+            assert (got == want).all(), "%s %s: %s" % (gen, op, _first_bad(got, want, a, b, c))
+
+
+GEN = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]
+
+
+def test_generated_formats_match_the_build_list():
+    from paper_1602_04716_gb300 import build
+    assert sorted(build.GEN_FORMATS) == sorted(GEN)
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_generated_netlist_exhaustive_1_4_3(op, rnd):
+    a, b = synth.all_pairs(8)
+    a, b = a.astype(np.uint32), b.astype(np.uint32)
+    got = circuit(4, 3, rnd, op, a, b, generated=True)
+    want = oracle.binop(op, 4, 3, rnd, a, b)
+    assert (got == want).all(), _first_bad(got, want, a, b)
+
+
+@pytest.mark.parametrize("E,M", GEN)
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_generated_netlist_sampled(E, M, rnd):
+    n = 1 << 14
+    B = 1 + E + M
+    for gen in ("fp", "bits"):
+        if gen == "fp":
+            a, b, c = (synth.fp_values(E, M, n, s).astype(np.uint32) for s in (41, 42, 43))
+        else:
+            a, b, c = (synth.uniform_bits(B, n, s).astype(np.uint32) for s in (51, 52, 53))
+        for op in OPS:
+            got = circuit(E, M, rnd, op, a, b, c, generated=True)
             want = oracle.binop(op, E, M, rnd, a, b, c)
             assert (got == want).all(), "%s %s: %s" % (gen, op, _first_bad(got, want, a, b, c))
