@@ -131,31 +131,28 @@ def lop3_rate(bs, torch) -> float:
 
 
 def cpu_baseline(target_s: float = 12.0):
-    """The oracle, as it stands, on a bounded sample of the workload."""
+    """The oracle, as it stands, on a bounded sample of the workload: the first
+    2^26 elements of each of the four (format, op) vectors, passed over
+    repeatedly until about target_s seconds of oracle time have been spent."""
     import oracle
-    per = []
-    m = 1 << 18
+    m = min(N, 1 << 26)
+    data = {}
     for E, M in FORMATS:
-        a = synth.fp_values(E, M, m, synth.SEED_A).astype(np.uint32)
-        b = synth.fp_values(E, M, m, synth.SEED_B).astype(np.uint32)
-        for op in OPS:
-            t = time.perf_counter()
-            oracle.binop(op, E, M, RND, a, b)
-            per.append(time.perf_counter() - t)
-    # scale the sample so the timed pass takes about target_s
-    m2 = int(min(1 << 24, max(m, m * target_s / max(sum(per), 1e-6))))
-    tot, els = 0.0, 0
-    for E, M in FORMATS:
-        a = synth.fp_values(E, M, m2, synth.SEED_A).astype(np.uint32)
-        b = synth.fp_values(E, M, m2, synth.SEED_B).astype(np.uint32)
-        for op in OPS:
-            t = time.perf_counter()
-            oracle.binop(op, E, M, RND, a, b)
-            tot += time.perf_counter() - t
-            els += m2
+        data[(E, M)] = (synth.fp_values(E, M, m, synth.SEED_A).astype(np.uint32),
+                        synth.fp_values(E, M, m, synth.SEED_B).astype(np.uint32))
+    tot, els, passes = 0.0, 0, 0
+    while tot < target_s or passes == 0:
+        for E, M in FORMATS:
+            a, b = data[(E, M)]
+            for op in OPS:
+                t = time.perf_counter()
+                oracle.binop(op, E, M, RND, a, b)
+                tot += time.perf_counter() - t
+                els += m
+        passes += 1
     return {"value": els / tot, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "first %d elements of each of the 4 (format, op) vectors of the workload "
-                      "(same seeds), %.1f s of oracle time" % (m2, tot)}
+            "sample": "first %d elements of each of the 4 (format, op) vectors of the workload (same seeds), "
+                      "%d passes, %.1f s of oracle time" % (m, passes, tot)}
 
 
 def run_reference(args):
@@ -314,6 +311,10 @@ def run_gpu(args):
     if args.serve_seconds > 0:
         serving = run_serving(bs, torch, args, rank)
 
+    sweep = None
+    if args.sweep_n > 0:
+        sweep = run_sweep(bs, torch, args, rank, hbm, L)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -328,7 +329,8 @@ def run_gpu(args):
                            "seeds": [synth.SEED_A, synth.SEED_B], "parallelism": "dp%d" % world,
                            "tuned_shapes_applied": tuned},
                 "roofline": roof, "kernels": kinfo, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-                "cpu_baseline": cpu, "batched": batched, "serving": serving}
+                "cpu_baseline": cpu, "batched": batched, "serving": serving,
+                "format_sweep": sweep}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -461,6 +463,60 @@ def run_serving(bs, torch, args, rank):
     return out
 
 
+def run_sweep(bs, torch, args, rank, hbm, L):
+    """Format sweep: every 1/E/M with E in 3..8 and M in 2..23, n elements,
+    bs_add, bs_mul and fma2 (RN), operands from the same value recipe.  Per
+    launch: CUDA-event time (median of 3 after one warm-up), HBM GB/s of the
+    algorithmic bytes, logic-op rate from the gate count, and the fraction of
+    the roofline min(HBM peak / bytes per element, 32 * L / G)."""
+    n = args.sweep_n
+    stream = torch.cuda.current_stream()
+    rows = []
+    for E in range(3, 9):
+        for M in range(2, 24):
+            f = bs.Format(E, M, RND)
+            B = 1 + E + M
+            std = bs.empty_standard(f, n)
+            ops_ = []
+            for seed in (synth.SEED_A, synth.SEED_B, synth.SEED_C):
+                bs.bsfp_synth_fp_values(f, n, seed, rank, 0, std)
+                p = bs.empty_bitslice(f, n)
+                bs.bsfp_pack(f, std, n, p)
+                ops_.append(p)
+            out = bs.empty_bitslice(f, n)
+            for op in ("add", "mul", "fma2"):
+                ts = []
+                for k in range(4):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    bs.bsfp_op(op, f, ops_[0], ops_[1], out, n, c=ops_[2], stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if k:
+                        ts.append(e0.elapsed_time(e1) * 1e-3)
+                t = float(np.median(ts))
+                nin = 3 if op == "fma2" else 2
+                bpe = (nin + 1) * B / 8
+                G = bs.bsfp_gate_count(f, op)
+                r_hbm = hbm * 1e9 / bpe
+                r_alu = L * 32 / G
+                rows.append({"fmt": "1/%d/%d" % (E, M), "op": op, "ms": t * 1e3, "elements_per_s": n / t,
+                             "hbm_gbs": n * bpe / t / 1e9, "gates_per_word": G,
+                             "logic_frac": G * n / 32 / t / L, "bound": "hbm" if r_hbm <= r_alu else "alu",
+                             "frac": (n / t) / min(r_hbm, r_alu)})
+            del ops_, out, std
+    summary = {"formats": len(rows) // 3, "elements": n, "rounding": "RN"}
+    for op in ("add", "mul", "fma2"):
+        fr = np.array([r["frac"] for r in rows if r["op"] == op])
+        summary[op] = {"frac_min": float(fr.min()), "frac_median": float(np.median(fr)), "frac_max": float(fr.max()),
+                       "alu_bound_formats": sum(1 for r in rows if r["op"] == op and r["bound"] == "alu")}
+    if args.sweep_out:
+        with open(args.sweep_out, "w") as fh:
+            json.dump({"summary": summary, "rows": rows}, fh, indent=1)
+        summary["table"] = args.sweep_out
+    return summary
+
+
 def run_e2e(bs, torch, n, rank, args):
     """Per step: pinned host standard arrays -> device -> pack -> add, mul ->
     unpack -> host, for both formats, all through the library's C ABI."""
@@ -542,6 +598,9 @@ def main(argv=None):
     ap.add_argument("--serve-saturated", type=int, default=20000, help="requests in the saturated run")
     ap.add_argument("--serve-pool", type=int, default=2048, help="device-resident operand pairs")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--sweep-n", type=int, default=1 << 26,
+                    help="elements per vector in the format sweep (0 skips it)")
+    ap.add_argument("--sweep-out", default=None, help="write the full sweep table (JSON) here")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

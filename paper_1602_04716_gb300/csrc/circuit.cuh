@@ -60,6 +60,24 @@ template <class W> BSFP_HD W OR3(W a, W b, W c) { return a | b | c; }
 template <class W> BSFP_HD W AND3(W a, W b, W c) { return a & b & c; }
 template <class W> BSFP_HD W ANDOR(W a, W b, W c) { return (a & b) | c; }  /* a&b | c       */
 template <class W> BSFP_HD W ANDNN(W a, W b, W c) { return a & ~b & ~c; }  /* a & !b & !c   */
+/* The full-adder gates as single instructions: on the device, for 32-bit
+ * words, XOR3 and MAJ are emitted as lop3.b32 with their truth tables, so the
+ * compiler cannot regroup them (left to itself it may share x^y between the
+ * sum and a majority rewritten as (x&y)|(z&(x^y)), which costs four
+ * instructions per full adder instead of two).  Only for inputs that are
+ * never constants: a constant input would no longer fold away. */
+#if defined(__CUDA_ARCH__)
+template <unsigned L>
+__device__ __forceinline__ uint32_t lop3_hard(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(L));
+    return d;
+}
+__device__ __forceinline__ uint32_t XOR3H(uint32_t a, uint32_t b, uint32_t c) { return lop3_hard<0x96u>(a, b, c); }
+__device__ __forceinline__ uint32_t MAJH(uint32_t a, uint32_t b, uint32_t c) { return lop3_hard<0xE8u>(a, b, c); }
+#endif
+template <class W> BSFP_HD W XOR3H(W a, W b, W c) { return XOR3(a, b, c); }
+template <class W> BSFP_HD W MAJH(W a, W b, W c) { return MAJ(a, b, c); }
 /* Any function of three words, given by its truth table L: bit (4a+2b+c) of L
  * is the output for input bits a, b, c (the LOP3 immediate convention). */
 template <unsigned L, class W> BSFP_HD W F3(W a, W b, W c) {
@@ -331,38 +349,47 @@ BSFP_HD void fp_add(const W* a, const W* b, W* r) {
 }
 
 /* ------------------------------------------------------------------ mul --- */
-/* P = A * B for n-bit unsigned A, B: carry-save array, one row per bit of B,
- * then a ripple adder for the upper half (Sec. 4: the significand product is
- * unrolled and kept in registers). */
+/* P = A * B for n-bit unsigned A, B (n >= 2): carry-save array, one row per
+ * bit of B, then a ripple adder for the upper half (Sec. 4: the significand
+ * product is unrolled and kept in registers).  After row j the sums S cover
+ * columns 0..n+j-1 and the carries C columns j+1..j+n-1; the last cell of
+ * every row has no sum or carry to add and passes its partial product
+ * through, and row 1 has no carries yet (half adders), so every full adder
+ * below has three variable inputs. */
 template <int n, class W> BSFP_HD void umul(const W* A, const W* Bv, W* P) {
     W S[2 * n], C[2 * n];
-    BSFP_UNROLL
-    for (int w = 0; w < 2 * n; ++w) S[w] = C[w] = W(0u);
     BSFP_UNROLL
     for (int i = 0; i < n; ++i) S[i] = AND(A[i], Bv[0]);
     BSFP_UNROLL
     for (int j = 1; j < n; ++j) {
         W nc[2 * n];
         BSFP_UNROLL
-        for (int i = 0; i < n; ++i) {
+        for (int i = 0; i < n - 1; ++i) {
             const int w = i + j;
             const W pp = AND(A[i], Bv[j]);
-            const W s = XOR3(S[w], C[w], pp);
-            nc[w + 1] = MAJ(S[w], C[w], pp);
-            S[w] = s;
+            if (j == 1) {
+                nc[w + 1] = AND(S[w], pp);
+                S[w] = XOR(S[w], pp);
+            } else {
+                nc[w + 1] = MAJH(S[w], C[w], pp);
+                S[w] = XOR3H(S[w], C[w], pp);
+            }
         }
-        C[j] = W(0u);
+        S[n - 1 + j] = AND(A[n - 1], Bv[j]);
         BSFP_UNROLL
-        for (int i = 0; i < n; ++i) C[i + j + 1] = nc[i + j + 1];
+        for (int i = 0; i < n - 1; ++i) C[i + j + 1] = nc[i + j + 1];
     }
     BSFP_UNROLL
     for (int w = 0; w < n; ++w) P[w] = S[w];
-    W c = W(0u);
+    /* columns n..2n-2 hold S and C; column 2n-1 only the final carry */
+    W c = AND(S[n], C[n]);
+    P[n] = XOR(S[n], C[n]);
     BSFP_UNROLL
-    for (int w = n; w < 2 * n; ++w) {
-        P[w] = XOR3(S[w], C[w], c);
-        c = MAJ(S[w], C[w], c);
+    for (int w = n + 1; w < 2 * n - 1; ++w) {
+        P[w] = XOR3H(S[w], C[w], c);
+        c = MAJH(S[w], C[w], c);
     }
+    P[2 * n - 1] = c;
 }
 
 /* r = a * b, one rounding (Sec. 4, Table 1, Mul). */
