@@ -518,9 +518,11 @@ def run_sweep(bs, torch, args, rank, hbm, L):
 
 
 def run_e2e(bs, torch, n, rank, args):
-    """Per step: pinned host standard arrays -> device -> pack -> add, mul ->
-    unpack -> host, for both formats, all through the library's C ABI."""
-    host_in, dev_std, dev_pl, host_out = {}, {}, {}, {}
+    """Per step, for both formats: the two operand vectors in page-locked host
+    memory (standard form) through bsfp_pipeline_run -- chunked copy in, pack,
+    bs_add and bs_mul, unpack, copy out over rotating streams -- into two
+    result vectors in page-locked host memory."""
+    host_in, host_out = {}, {}
     for E, M in FORMATS:
         f = bs.Format(E, M, RND)
         ins = []
@@ -532,11 +534,9 @@ def run_e2e(bs, torch, n, rank, args):
             ins.append(h)
             del d
         host_in[(E, M)] = ins
-        dev_std[(E, M)] = [bs.empty_standard(f, n) for _ in range(2)]
-        dev_pl[(E, M)] = [bs.empty_bitslice(f, n) for _ in range(3)]
         host_out[(E, M)] = [torch.empty(n, dtype=ins[0].dtype, pin_memory=True) for _ in OPS]
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
+    pipe = bs.Pipeline(args.e2e_chunk, args.e2e_depth)
     h2d = d2h = 0
 
     def step():
@@ -544,36 +544,26 @@ def run_e2e(bs, torch, n, rank, args):
         h2d = d2h = 0
         for E, M in FORMATS:
             f = bs.Format(E, M, RND)
-            (ha, hb), (da, db), (pa, pb, po) = host_in[(E, M)], dev_std[(E, M)], dev_pl[(E, M)]
-            da.copy_(ha, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            h2d += ha.numel() * ha.element_size() * 2
-            bs.bsfp_pack(f, da, n, pa, stream=stream)
-            bs.bsfp_pack(f, db, n, pb, stream=stream)
-            for j, op in enumerate(OPS):
-                bs.bsfp_op(op, f, pa, pb, po, n, stream=stream)
-                bs.bsfp_unpack(f, po, n, da, stream=stream)
-                host_out[(E, M)][j].copy_(da, non_blocking=True)
-                d2h += da.numel() * da.element_size()
-                # da is reused: the next unpack waits for this copy on the same stream
+            (ha, hb), outs = host_in[(E, M)], host_out[(E, M)]
+            pipe.run(f, OPS, ha, hb, outs, n)
+            h2d += 2 * ha.numel() * ha.element_size()
+            d2h += sum(o.numel() * o.element_size() for o in outs)
 
     for _ in range(max(1, min(args.warmup, 2))):
         step()
     torch.cuda.synchronize()
     k = max(1, args.e2e_steps)
     t = time.perf_counter()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
     for _ in range(k):
         step()
-    e1.record(stream)
     torch.cuda.synchronize()
-    wall = (time.perf_counter() - t) / k
-    dev_ms = e0.elapsed_time(e1) / k
-    sec = max(wall, dev_ms * 1e-3)
+    sec = (time.perf_counter() - t) / k
+    pipe.close()
     return {"value": len(FORMATS) * len(OPS) * n / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k,
-            "path": "pinned host -> H2D -> bsfp_pack -> bsfp_add/bsfp_mul -> bsfp_unpack -> D2H, per format"}
+            "path": "pinned host -> bsfp_pipeline_run (chunks of %d over %d streams: H2D, bsfp_pack, "
+                    "bsfp_add + bsfp_mul, bsfp_unpack, D2H) -> pinned host, per format"
+                    % (args.e2e_chunk or (1 << 23), args.e2e_depth or 4)}
 
 
 def main(argv=None):
@@ -585,6 +575,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=N, help="elements per vector (default 2^28)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-chunk", type=int, default=0, help="pipeline chunk (elements; 0 = library default)")
+    ap.add_argument("--e2e-depth", type=int, default=0, help="pipeline streams (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=1 << 20,

@@ -202,6 +202,38 @@ bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t 
  * anything is launched. */
 bsfp_status bsfp_batch_run_noalloc(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s);
 
+/* ----------------------------------------------------- host-to-host path --- */
+/* Vectors in host memory, results to host memory: standard form in, the ops
+ * of Sec. 4 on the GPU, standard form out (not part of the paper: the
+ * transfer pipeline around its operations).  The vectors are cut into chunks
+ * that rotate over `depth` streams, each chunk copied to the device, packed,
+ * run through every requested op, unpacked and copied back, so that the
+ * copies in both directions overlap the kernels of other chunks; the inputs
+ * cross the host link once for all the ops.  Results are identical to packing
+ * the whole vectors and calling the ops once.
+ *
+ * The pipeline owns its streams and its device buffers (about
+ * 7 + nops buffers of one chunk per stream, allocated on first use and grown
+ * for wider formats or more ops).  One pipeline must not be run by two host
+ * threads at once. */
+typedef struct bsfp_pipeline_st* bsfp_pipeline;
+
+#define BSFP_PIPE_MAX_OPS 4
+
+/* chunk: elements per chunk, a multiple of 1024 in [1024, 2^30] (0 = 2^23);
+ * depth: streams, 1..16 (0 = 4).  Created on the current device. */
+bsfp_status bsfp_pipeline_create(int64_t chunk, int32_t depth, bsfp_pipeline* out);
+/* outs[q][i] = ops[q](a[i], b[i] [, c[i]]) for i < n, q < nops (1..4; c is
+ * read only when some op is BSFP_OP_FMA2).  a, b, c, outs[q]: standard
+ * arrays (containers of bsfp_container_bytes(f)) in host memory; page-locked
+ * memory lets the copies run asynchronously, pageable memory works but its
+ * copies are staged by the driver and overlap less.  Blocks until every
+ * result is in host memory.  Errors: as the single ops, before any copy;
+ * CUDA failures BSFP_ERR_CUDA. */
+bsfp_status bsfp_pipeline_run(bsfp_pipeline p, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,
+                              const void* b, const void* c, void* const* outs, int64_t n);
+void bsfp_pipeline_free(bsfp_pipeline p);
+
 /* -------------------------------------------------------------- serving --- */
 /* A request server for element-wise ops on device-resident bitslice operands
  * (not part of the paper: a serving form of the Sec. 4 operations).  Requests

@@ -125,6 +125,9 @@ def _lib():
                 "bsfp_batch_free": (None, [p]),
                 "bsfp_launch_jobs": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
                 "bsfp_batch_run_noalloc": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
+                "bsfp_pipeline_create": (i32, [i64, i32, ctypes.POINTER(p)]),
+                "bsfp_pipeline_run": (i32, [p, F, i32, ctypes.POINTER(i32), p, p, p, ctypes.POINTER(p), i64]),
+                "bsfp_pipeline_free": (None, [p]),
                 "bsfp_server_create": (i32, [ctypes.POINTER(bsfp_server_options), ctypes.POINTER(p)]),
                 "bsfp_server_submit": (i32, [p, ctypes.POINTER(bsfp_job), ctypes.POINTER(i64)]),
                 "bsfp_server_poll": (i32, [p, ctypes.POINTER(bsfp_completion), i32]),
@@ -309,6 +312,47 @@ def bsfp_batch_run_noalloc(jobs, njobs: int, stream=None):
     """The batched launch with its scratch in the library's fixed device array
     (no allocation); for callers that must not allocate device memory."""
     _check(_lib().bsfp_batch_run_noalloc(jobs, njobs, _stream(stream)), "bsfp_batch_run_noalloc")
+
+
+# ---------------------------------------------------- host-to-host path ---
+PIPE_MAX_OPS = 4
+
+
+def _host_ptr(x):
+    """Address of a host array: a CPU torch tensor or a numpy array."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert not x.is_cuda, "host-to-host path: pass host arrays"
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+class Pipeline:
+    """Owns a bsfp_pipeline: standard arrays in host memory through the GPU
+    path and back, in chunks over several streams."""
+
+    def __init__(self, chunk: int = 0, depth: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(_lib().bsfp_pipeline_create(chunk, depth, ctypes.byref(self._h)), "bsfp_pipeline_create")
+
+    def run(self, f, ops, a, b, outs, n: int, c=None):
+        ops = [OPS.get(o, o) for o in ops]
+        arr = (ctypes.c_int32 * len(ops))(*ops)
+        optr = (ctypes.c_void_p * len(outs))(*[_host_ptr(o) for o in outs])
+        _check(_lib().bsfp_pipeline_run(self._h, _fmt(f), len(ops), arr, _host_ptr(a), _host_ptr(b),
+                                        _host_ptr(c), optr, n), "bsfp_pipeline_run")
+
+    def close(self):
+        if self._h:
+            _lib().bsfp_pipeline_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------------------- serving ---

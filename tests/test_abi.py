@@ -145,3 +145,16 @@ def test_noalloc_sizes_rejected_before_any_cuda_call():
     assert L.bsfp_batch_run_noalloc(jobs, bs.NOALLOC_MAX_JOBS + 1, None) == bs.ERR_SIZE
     assert L.bsfp_batch_run_noalloc(jobs, -1, None) == bs.ERR_SIZE
     assert L.bsfp_batch_run_noalloc(jobs, 0, None) == bs.OK
+
+
+def test_pipeline_arguments_validated_before_any_cuda_call():
+    L = _binding._lib()
+    h = ctypes.c_void_p()
+    for chunk, depth in ((1000, 2), (-1024, 2), (1 << 31, 2), (4096, 17), (4096, -1)):
+        assert L.bsfp_pipeline_create(chunk, depth, ctypes.byref(h)) == bs.ERR_SIZE
+        assert not h.value
+    assert L.bsfp_pipeline_create(4096, 2, None) == bs.ERR_NULL
+    ops = (ctypes.c_int32 * 1)(0)
+    outs = (ctypes.c_void_p * 1)(256)
+    assert L.bsfp_pipeline_run(None, bs.Format(4, 3), 1, ops, 256, 256, None, outs, 10) == bs.ERR_NULL
+    L.bsfp_pipeline_free(None)

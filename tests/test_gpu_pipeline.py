@@ -1,0 +1,82 @@
+"""The host-to-host pipeline: standard arrays in host memory, every chunk
+copied in, packed, run through each requested op, unpacked and copied back
+over rotating streams.  Results must equal the oracle bit for bit, for
+lengths that end mid-chunk and mid-word, for pageable and page-locked host
+arrays, and for several ops sharing one transfer of the inputs."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_1602_04716_gb300 as bs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _host(E, M, n, seed, pinned):
+    x = synth.fp_values(E, M, n, seed)
+    if not pinned:
+        return x
+    t = torch.empty(n, dtype={1: torch.uint8, 2: torch.int16, 4: torch.int32}[x.itemsize], pin_memory=True)
+    t.numpy()[:] = x.view(t.numpy().dtype)
+    return t
+
+
+def _np(x, dtype):
+    return x.numpy().view(dtype) if hasattr(x, "numpy") else x
+
+
+@pytest.mark.parametrize("E,M", [(4, 3), (5, 7), (8, 23), (6, 9)])
+@pytest.mark.parametrize("pinned", [False, True])
+def test_pipeline_matches_oracle(E, M, pinned):
+    pipe = bs.Pipeline(chunk=4096, depth=3)
+    dt = synth.container_dtype(1 + E + M)
+    for n in (1, 1000, 4096, 4097, 50_001):
+        for rnd in (0, 1):
+            f = bs.Format(E, M, rnd)
+            a, b, c = (_host(E, M, n, 100 * n + s, pinned) for s in (1, 2, 3))
+            ops = ["add", "sub", "mul", "fma2"]
+            outs = [_host(E, M, n, 0, pinned) for _ in ops]
+            pipe.run(f, ops, a, b, outs, n, c=c)
+            av, bv, cv = (_np(x, dt).astype(np.uint32) for x in (a, b, c))
+            for op, o in zip(ops, outs):
+                want = oracle.binop(op, E, M, rnd, av, bv, cv)
+                got = _np(o, dt).astype(np.uint32)
+                assert (got == want).all(), "%s 1/%d/%d rnd=%d n=%d" % (op, E, M, rnd, n)
+    pipe.close()
+
+
+def test_pipeline_default_chunks_and_growth():
+    """A long vector in default-sized chunks, then a wider format that makes
+    the pipeline grow its buffers."""
+    pipe = bs.Pipeline()
+    for E, M, n in ((4, 4, (1 << 24) + 12345), (8, 23, 300_000)):
+        f = bs.Format(E, M, 0)
+        a, b = (_host(E, M, n, s, True) for s in (7, 8))
+        out = _host(E, M, n, 0, True)
+        pipe.run(f, ["mul"], a, b, [out], n)
+        dt = synth.container_dtype(1 + E + M)
+        idx = np.unique(np.concatenate([np.arange(0, n, 9973), [n - 1]]))
+        av, bv = (_np(x, dt)[idx].astype(np.uint32) for x in (a, b))
+        want = oracle.binop("mul", E, M, 0, av, bv)
+        assert (_np(out, dt)[idx].astype(np.uint32) == want).all()
+    pipe.close()
+
+
+def test_pipeline_validation():
+    pipe = bs.Pipeline(chunk=1024, depth=2)
+    f = bs.Format(4, 3)
+    a = np.zeros(10, np.uint8)
+    with pytest.raises(bs.BsfpError) as ei:
+        pipe.run(f, [], a, a, [], 10)
+    assert ei.value.status == bs.ERR_SIZE
+    with pytest.raises(bs.BsfpError) as ei:
+        pipe.run(f, ["fma2"], a, a, [a.copy()], 10)
+    assert ei.value.status == bs.ERR_NULL
+    with pytest.raises(bs.BsfpError) as ei:
+        pipe.run(f, [9], a, a, [a.copy()], 10)
+    assert ei.value.status == bs.ERR_UNSUPPORTED
+    pipe.run(f, ["add"], a, a, [a.copy()], 0)   # n == 0: nothing to do
+    pipe.close()
