@@ -47,10 +47,11 @@ RND = 0
 WORKLOAD = ("plain single-format at scale: bs_add + bs_mul (RN) on 1/4/4 and 1/5/7, "
             "2^28 elements per vector, operands resident in bitslice form")
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from an ncu capture (profiles/), keyed by (E, M, op); None until the
-# kernel as it now stands has been captured.
-NCU_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per 2^28-element launch, keyed
+# by (E, M, op), from the ncu capture of the kernel as it now stands at 2^26
+# elements scaled by 4 (profiles/binop_1_5_7_add_mul_full_2p26.md); a kernel
+# not listed, or changed since its capture, reports null.
+NCU_TRAFFIC = {(5, 7, "mul"): (218.150656e6 + 70.085376e6) * 4, (5, 7, "add"): (218.121216e6 + 71.256576e6) * 4}
 
 
 def apply_tuning() -> int:
@@ -293,7 +294,7 @@ def run_gpu(args):
         roof = {"bound": "alu", "achieved": d["logic_tops"], "peak": L / 1e12, "unit": "Tops/s",
                 "frac": d["logic_tops"] * 1e12 / L,
                 "peak_source": "measured LOP3 issue rate (bsfp_lop3_probe, this run)"}
-    tr = NCU_TRAFFIC.get((E, M, op))
+    tr = NCU_TRAFFIC.get((E, M, op)) if n == N else None
     roof.update({"kernel": d["kernel"], "traffic": tr,
                  "algorithmic_bytes": 3 * B * n / 8, "gate_ops": d["gates_per_word"] * ((n + 31) // 32),
                  "hbm_peak_gbs": hbm, "logic_peak_tops": L / 1e12})
