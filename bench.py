@@ -157,7 +157,7 @@ def cpu_baseline(target_s: float = 12.0):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    rank = dist_env()[0]
     if rank != 0:
         return 0
     import oracle
@@ -192,14 +192,35 @@ def run_reference(args):
     return 0
 
 
+def dist_env():
+    """(rank, world size, local rank) from the launcher's environment."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, dist, world: int, device) -> float:
+    """The largest of the ranks' values (the job ends when its slowest rank
+    does); the value itself when there is one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, elements_per_rank_step: float, ms_per_step: float) -> float:
+    """Whole-job elements/s: every rank processes its own elements (weak
+    scaling, no exchange between ranks)."""
+    return world * elements_per_rank_step / (ms_per_step * 1e-3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
     import paper_1602_04716_gb300 as bs
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -256,13 +277,9 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    ms = t0.elapsed_time(t1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(t0.elapsed_time(t1), dist, world, "cuda")
     ms_step = ms_max / args.steps
-    value = world * len(kern) * n / (ms_step * 1e-3)
+    value = job_throughput(world, len(kern) * n, ms_step)
 
     # ---- per-kernel roofline ----
     kinfo = []
@@ -312,6 +329,8 @@ def run_gpu(args):
     if args.serve_seconds > 0:
         serving = run_serving(bs, torch, args, rank)
 
+    small = run_small_case(bs, torch, rank) if args.sweep_n > 0 else None
+
     sweep = None
     if args.sweep_n > 0:
         sweep = run_sweep(bs, torch, args, rank, hbm, L)
@@ -331,7 +350,7 @@ def run_gpu(args):
                            "tuned_shapes_applied": tuned},
                 "roofline": roof, "kernels": kinfo, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
                 "cpu_baseline": cpu, "batched": batched, "serving": serving,
-                "format_sweep": sweep}
+                "format_sweep": sweep, "small_case": small}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -423,8 +442,10 @@ def run_serving(bs, torch, args, rank):
     arr, nj, keep, _, _ = batched_workload(bs, torch, pool, 256, 1 << 22, 19700101, rank)
     src = [arr[i] for i in range(nj)]
     out = {}
-    for name, rate, nreq in (("poisson", args.serve_rate, int(args.serve_rate * args.serve_seconds)),
-                             ("saturated", None, args.serve_saturated)):
+    runs = (("poisson", args.serve_rate, int(args.serve_rate * args.serve_seconds), 64 << 30),
+            ("poisson_small_budget", args.serve_rate, int(args.serve_rate * 2), args.serve_small_budget),
+            ("saturated", None, args.serve_saturated, 64 << 30))
+    for name, rate, nreq, budget in runs:
         pick = synth.splitmix64(424242 + int(rate or 0), nreq, 2 * rank)
         jobs = (bs.bsfp_job * nreq)()
         elems = 0
@@ -437,9 +458,9 @@ def run_serving(bs, torch, args, rank):
             arrival = np.cumsum(gaps * 1e9).astype(np.int64)
         else:
             arrival = np.zeros(nreq, dtype=np.int64)
-        srv = bs.Server(64 << 30, slots=args.serve_slots)
-        # warm-up: a short slice of the same trace
-        w = min(nreq, 256)
+        srv = bs.Server(budget, slots=args.serve_slots)
+        # warm-up: the first second of the same trace (at most 20,000 requests)
+        w = min(nreq, int(rate or 20000))
         srv.replay(jobs, w, arrival[:w] - arrival[0], release=True)
         done = srv.replay(jobs, nreq, arrival, release=True, timeout_ms=120000)
         st = srv.stats()
@@ -452,15 +473,56 @@ def run_serving(bs, torch, args, rank):
                      "achieved_requests_per_s": nreq / span, "elements_per_s": elems / span,
                      "latency_us": {"p50": float(np.percentile(lat_us, 50)), "p99": float(np.percentile(lat_us, 99)),
                                     "p999": float(np.percentile(lat_us, 99.9)), "max": float(lat_us.max())},
-                     "micro_batches": st["batches"],
+                     "budget_bytes": budget, "micro_batches": st["batches"],
                      "peak_inflight_batches": st["peak_inflight_batches"],
                      "arena_peak_bytes": st["arena_peak_bytes"], "failed": st["failed"]}
-    out["workload"] = ("Poisson arrivals at %g requests/s for %g s (and a saturated run of %d requests arriving "
-                       "at once); bs_add/bs_mul 50/50, RN; lengths log-uniform in [256, 4194304]; formats %s uniform; "
-                       "operands drawn from %d device-resident pairs; results from a 64 GB budget; %d slots"
-                       % (args.serve_rate, args.serve_seconds, args.serve_saturated,
+    out["workload"] = ("Poisson arrivals at %g requests/s for %g s after a 1 s warm-up, results from a 64 GB "
+                       "budget (and the same arrivals for 2 s under a %d MB budget, and a saturated run of %d "
+                       "requests arriving at once); bs_add/bs_mul 50/50, RN; lengths log-uniform in [256, 4194304]; "
+                       "formats %s uniform; operands drawn from %d device-resident pairs; %d slots"
+                       % (args.serve_rate, args.serve_seconds, args.serve_small_budget >> 20, args.serve_saturated,
                           ["1/%d/%d" % fm for fm in BATCH_FORMATS], pool, args.serve_slots))
     del keep
+    return out
+
+
+def run_small_case(bs, torch, rank):
+    """The 8-bit format 1/4/3 on all 65,536 operand pairs (a = i >> 8,
+    b = i & 255): bs_add and bs_mul, RN and RZ, plus the pack/unpack round
+    trip, as single launches; too small for a roofline, so latency only."""
+    import oracle  # noqa: F401  (the pairs are built here; parity is checked by the tests)
+    n = 1 << 16
+    i = np.arange(n, dtype=np.uint32)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for rnd in (0, 1):
+        f = bs.Format(4, 3, rnd)
+        std = [torch.from_numpy(x.astype(np.uint8)).cuda() for x in (i >> 8, i & 255)]
+        planes = [bs.empty_bitslice(f, n) for _ in range(3)]
+        back = bs.empty_standard(f, n)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(20):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e3)
+            return float(np.median(ts))
+
+        r = "RZ" if rnd else "RN"
+        out["pack_us"] = timed(lambda: bs.bsfp_pack(f, std[0], n, planes[0], stream=stream))
+        bs.bsfp_pack(f, std[1], n, planes[1], stream=stream)
+        for op in ("add", "mul"):
+            out["%s_%s_us" % (op, r)] = timed(lambda: bs.bsfp_op(op, f, planes[0], planes[1], planes[2], n,
+                                                                 stream=stream))
+        out["unpack_us"] = timed(lambda: bs.bsfp_unpack(f, planes[0], n, back, stream=stream))
+        assert torch.equal(back, std[0])
+    out["workload"] = "1/4/3, all 65,536 operand pairs, single launches (median of 20, CUDA events)"
     return out
 
 
@@ -586,7 +648,8 @@ def main(argv=None):
                     help="vectors in the batched comparison (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-wpt", type=int, default=0)
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="Poisson serving run length (0 skips it)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="Poisson serving run length (0 skips it)")
+    ap.add_argument("--serve-small-budget", type=int, default=16 << 20, help="bytes, the back-pressure run")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="requests/s")
     ap.add_argument("--serve-saturated", type=int, default=20000, help="requests in the saturated run")
     ap.add_argument("--serve-pool", type=int, default=2048, help="device-resident operand pairs")
