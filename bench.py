@@ -417,7 +417,9 @@ def run_batched(bs, torch, args, rank, hbm):
         return e0.elapsed_time(e1) / steps, (bs.bsfp_launch_count() - l0) // steps
 
     variants = {}
-    persistent = bs.BatchPlan(arr, nj, bs.BATCH_PERSISTENT, args.batch_wpt)
+    from paper_1602_04716_gb300 import tune
+    wpt, bps = (args.batch_wpt, 0) if args.batch_wpt else tune.batch_shape()
+    persistent = bs.BatchPlan(arr, nj, bs.BATCH_PERSISTENT, wpt, bps)
     variants["persistent_graph"] = timed(lambda: persistent.run(stream), args.batch_steps)
     plain_graph = bs.BatchPlan(arr, nj, bs.BATCH_PLAIN)
     variants["plain_graph"] = timed(lambda: plain_graph.run(stream), args.batch_steps)

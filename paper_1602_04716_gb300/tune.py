@@ -45,6 +45,8 @@ def apply(path: str = CACHE) -> int:
     cache = load(path).get(gpu_name(), {})
     n = 0
     for key, v in cache.items():
+        if key.count("/") != 3:
+            continue   # not a per-format entry (the batched shape)
         e, m, r, op = key.split("/")
         f = _b.Format(int(e), int(m), int(r))
         if v["wpt"] in _b.bsfp_variants_compiled(f, op):
@@ -84,3 +86,87 @@ def autotune(op, f, a, b, c, out, n, bps_choices=(0, 1, 2, 3, 4, 6, 8), reps=5, 
         cache.setdefault(gpu_name(), {})[_key(f, op)] = {"wpt": best[0], "bps": best[1], "ms": table[best], "n": n}
         save(cache, path)
     return best, table
+
+
+# ------------------------------------------------------- batched shape ---
+def batch_shape(path: str = CACHE):
+    """(wpt, blocks_per_sm) cached for the batched persistent kernels on this
+    GPU, or (0, 0) for the library defaults."""
+    v = load(path).get(gpu_name(), {}).get("batch")
+    return (v["wpt"], v["bps"]) if v else (0, 0)
+
+
+def autotune_batch(jobs, njobs: int, reps: int = 5, path: str | None = CACHE):
+    """Time persistent plans of the given jobs at every (wpt, blocks/SM) and
+    keep the fastest; returns (best, table)."""
+    import torch
+    s = torch.cuda.current_stream()
+    table = {}
+    for wpt in (1, 2):
+        for bps in (0, 1, 2, 3, 4):
+            plan = _b.BatchPlan(jobs, njobs, _b.BATCH_PERSISTENT, wpt, bps)
+            ts = []
+            for _ in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                plan.run(s)
+                e1.record(s)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            plan.free()
+            ts = sorted(ts[1:])
+            table[(wpt, bps)] = ts[len(ts) // 2]
+    best = min(table, key=table.get)
+    if path:
+        cache = load(path)
+        cache.setdefault(gpu_name(), {})["batch"] = {"wpt": best[0], "bps": best[1], "ms": table[best]}
+        save(cache, path)
+    return best, table
+
+
+# The formats of the benchmarks and of the batched kernels, and the paper's FP32.
+TUNED_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]
+
+
+def main(argv=None):
+    """Re-tune every launch shape on this GPU and write the cache:
+    python -m paper_1602_04716_gb300.tune [--n N] [--out PATH]."""
+    import argparse
+    import torch
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--n", type=int, default=1 << 28, help="elements per operand (the at-scale size)")
+    ap.add_argument("--out", default=CACHE)
+    args = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    for E, M in TUNED_FORMATS:
+        for rnd in (0, 1):
+            f = _b.Format(E, M, rnd)
+            # the circuits have no data-dependent branches: operand values do not change the timing
+            a, b, c = (torch.zeros(f.bits * _b.bsfp_plane_stride(args.n), dtype=torch.int32, device="cuda")
+                       for _ in range(3))
+            o = _b.empty_bitslice(f, args.n)
+            for op in ("add", "mul", "fma2"):
+                best, table = autotune(op, f, a, b, c, o, args.n, path=args.out)
+                print("1/%d/%d %s %s: wpt %d, blocks/SM %d (%.3f ms)" % (E, M, "RZ" if rnd else "RN", op, best[0],
+                                                                        best[1], table[best]), flush=True)
+            del a, b, c, o
+            torch.cuda.empty_cache()
+    # the batched kernels on a mixed workload of the five batched formats
+    import numpy as np
+    fmts = [fm for fm in TUNED_FORMATS if fm != (8, 23)]
+    rng = np.random.default_rng(1602)
+    specs, keep = [], []
+    for i in range(512):
+        E, M = fmts[i % len(fmts)]
+        f = _b.Format(E, M, 0)
+        n = int(np.exp(rng.uniform(np.log(1024), np.log(1 << 22))))
+        ops_ = [torch.zeros(f.bits * _b.bsfp_plane_stride(n), dtype=torch.int32, device="cuda") for _ in range(3)]
+        keep.append(ops_)
+        specs.append((f, "add" if i % 2 else "mul", ops_[0], ops_[1], None, ops_[2], n))
+    jobs, nj = _b.make_jobs(specs)
+    best, table = autotune_batch(jobs, nj, path=args.out)
+    print("batched: wpt %d, blocks/SM %d (%.3f ms)" % (best[0], best[1], table[best]), flush=True)
+
+
+if __name__ == "__main__":
+    main()
