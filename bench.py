@@ -359,6 +359,8 @@ def run_gpu(args):
 
 
 BATCH_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
+FTZ_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]   # compiled with flush to zero too
+MODE_NAMES = ["RN", "RZ", "RN_FTZ", "RZ_FTZ"]
 
 
 def batched_workload(bs, torch, njobs, lo, hi, seed, rank=0, formats=BATCH_FORMATS, ops=("add", "mul")):
@@ -530,51 +532,74 @@ def run_small_case(bs, torch, rank):
 
 def run_sweep(bs, torch, args, rank, hbm, L):
     """Format sweep: every 1/E/M with E in 3..8 and M in 2..23, n elements,
-    bs_add, bs_mul and fma2 (RN), operands from the same value recipe.  Per
-    launch: CUDA-event time (median of 3 after one warm-up), HBM GB/s of the
-    algorithmic bytes, logic-op rate from the gate count, and the fraction of
-    the roofline min(HBM peak / bytes per element, 32 * L / G)."""
+    bs_add, bs_mul and fma2 under RN and RZ (and both with flush to zero for
+    the formats compiled with it), operands from the same value
+    recipe.  Per launch: CUDA-event time (median of 3 after one warm-up), HBM
+    GB/s of the algorithmic bytes, logic-op rate from the gate count, and the
+    fraction of the roofline min(HBM peak / bytes per element, 32 * L / G).
+    The RZ/RN ratios of time and gate count per op are the paper's one
+    surviving quantitative claim (Sec. 5.2: RZ is markedly cheaper)."""
     n = args.sweep_n
     stream = torch.cuda.current_stream()
     rows = []
     for E in range(3, 9):
         for M in range(2, 24):
-            f = bs.Format(E, M, RND)
             B = 1 + E + M
-            std = bs.empty_standard(f, n)
+            f0 = bs.Format(E, M, 0)
+            std = bs.empty_standard(f0, n)
             ops_ = []
             for seed in (synth.SEED_A, synth.SEED_B, synth.SEED_C):
-                bs.bsfp_synth_fp_values(f, n, seed, rank, 0, std)
-                p = bs.empty_bitslice(f, n)
-                bs.bsfp_pack(f, std, n, p)
+                bs.bsfp_synth_fp_values(f0, n, seed, rank, 0, std)
+                p = bs.empty_bitslice(f0, n)
+                bs.bsfp_pack(f0, std, n, p)
                 ops_.append(p)
-            out = bs.empty_bitslice(f, n)
-            for op in ("add", "mul", "fma2"):
-                ts = []
-                for k in range(4):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    bs.bsfp_op(op, f, ops_[0], ops_[1], out, n, c=ops_[2], stream=stream)
-                    e1.record(stream)
-                    e1.synchronize()
-                    if k:
-                        ts.append(e0.elapsed_time(e1) * 1e-3)
-                t = float(np.median(ts))
-                nin = 3 if op == "fma2" else 2
-                bpe = (nin + 1) * B / 8
-                G = bs.bsfp_gate_count(f, op)
-                r_hbm = hbm * 1e9 / bpe
-                r_alu = L * 32 / G
-                rows.append({"fmt": "1/%d/%d" % (E, M), "op": op, "ms": t * 1e3, "elements_per_s": n / t,
-                             "hbm_gbs": n * bpe / t / 1e9, "gates_per_word": G,
-                             "logic_frac": G * n / 32 / t / L, "bound": "hbm" if r_hbm <= r_alu else "alu",
-                             "frac": (n / t) / min(r_hbm, r_alu)})
+            out = bs.empty_bitslice(f0, n)
+            modes = (0, 1, 2, 3) if (E, M) in FTZ_FORMATS else (0, 1)
+            for rnd in modes:
+                f = bs.Format(E, M, rnd)
+                for op in ("add", "mul", "fma2"):
+                    ts = []
+                    for k in range(4):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        bs.bsfp_op(op, f, ops_[0], ops_[1], out, n, c=ops_[2], stream=stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                        if k:
+                            ts.append(e0.elapsed_time(e1) * 1e-3)
+                    t = float(np.median(ts))
+                    nin = 3 if op == "fma2" else 2
+                    bpe = (nin + 1) * B / 8
+                    G = bs.bsfp_gate_count(f, op)
+                    r_hbm = hbm * 1e9 / bpe
+                    r_alu = L * 32 / G
+                    rows.append({"fmt": "1/%d/%d" % (E, M), "rnd": MODE_NAMES[rnd], "op": op, "ms": t * 1e3,
+                                 "elements_per_s": n / t, "hbm_gbs": n * bpe / t / 1e9, "gates_per_word": G,
+                                 "logic_frac": G * n / 32 / t / L, "bound": "hbm" if r_hbm <= r_alu else "alu",
+                                 "frac": (n / t) / min(r_hbm, r_alu)})
             del ops_, out, std
-    summary = {"formats": len(rows) // 3, "elements": n, "rounding": "RN"}
+    summary = {"formats": len({r["fmt"] for r in rows}), "elements": n}
+    for rnd in ("RN", "RZ"):
+        for op in ("add", "mul", "fma2"):
+            sel = [r for r in rows if r["op"] == op and r["rnd"] == rnd]
+            fr = np.array([r["frac"] for r in sel])
+            summary["%s_%s" % (op, rnd)] = {"frac_min": float(fr.min()), "frac_median": float(np.median(fr)),
+                                            "frac_max": float(fr.max()),
+                                            "alu_bound_formats": sum(1 for r in sel if r["bound"] == "alu")}
     for op in ("add", "mul", "fma2"):
-        fr = np.array([r["frac"] for r in rows if r["op"] == op])
-        summary[op] = {"frac_min": float(fr.min()), "frac_median": float(np.median(fr)), "frac_max": float(fr.max()),
-                       "alu_bound_formats": sum(1 for r in rows if r["op"] == op and r["bound"] == "alu")}
+        rn = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN"}
+        rz = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RZ"}
+        tr = np.array([rz[k]["ms"] / rn[k]["ms"] for k in rn])
+        gr = np.array([rz[k]["gates_per_word"] / rn[k]["gates_per_word"] for k in rn])
+        summary["rz_over_rn_%s" % op] = {"time_median": float(np.median(tr)), "time_min": float(tr.min()),
+                                         "gates_median": float(np.median(gr)), "gates_min": float(gr.min())}
+    # flush to zero against gradual underflow, on the formats compiled with it
+    for op in ("add", "mul", "fma2"):
+        pl = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN"}
+        fz = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN_FTZ"}
+        summary["ftz_over_rn_%s" % op] = {k: {"time": fz[k]["ms"] / pl[k]["ms"],
+                                              "gates": fz[k]["gates_per_word"] / pl[k]["gates_per_word"]}
+                                          for k in fz}
     if args.sweep_out:
         with open(args.sweep_out, "w") as fh:
             json.dump({"summary": summary, "rows": rows}, fh, indent=1)

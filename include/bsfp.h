@@ -51,14 +51,20 @@ extern "C" {
 struct CUstream_st;
 typedef struct CUstream_st* bsfp_stream_t;
 
-/* Rounding (Sec. 4): round to nearest, ties to even; round toward zero. */
-typedef enum { BSFP_RN = 0, BSFP_RZ = 1 } bsfp_round;
+/* Rounding (Sec. 4): round to nearest, ties to even; round toward zero.
+ * The _FTZ modes add flush to zero (not in the paper; the optional mode that
+ * trades gradual underflow for fewer gates): an operand whose exponent field
+ * is 0 is read as a zero of its sign, and a result whose exact magnitude is
+ * below the smallest normal (tiny before rounding) is a zero of its sign.
+ * The _FTZ modes are compiled for 1/4/3, 1/4/4, 1/5/7, 1/5/10, 1/8/7 and
+ * 1/8/23; other formats return BSFP_ERR_UNSUPPORTED for them. */
+typedef enum { BSFP_RN = 0, BSFP_RZ = 1, BSFP_RN_FTZ = 2, BSFP_RZ_FTZ = 3 } bsfp_round;
 
 /* Format 1/E/M with rounding mode.  Passed by value. */
 typedef struct {
     int32_t exp_bits; /* E, 2..8 */
     int32_t man_bits; /* M, 1..23 */
-    int32_t rnd;      /* bsfp_round */
+    int32_t rnd;      /* bsfp_round: 0..3 */
 } bsfp_format;
 
 typedef enum {

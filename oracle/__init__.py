@@ -34,7 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 OPS = {"add": 0, "sub": 1, "mul": 2, "fma2": 3}
-RN, RZ = 0, 1
+RN, RZ, RN_FTZ, RZ_FTZ = 0, 1, 2, 3   # rounding modes; bit 1 = flush to zero
 
 
 def build(force: bool = False) -> str:

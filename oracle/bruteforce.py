@@ -13,6 +13,11 @@ significands it
    overflow (RN: to infinity once the magnitude reaches max + half an ulp;
    RZ: to the largest finite value) and IEEE signed zeros.
 
+With flush to zero (rounding modes 2 = RN and 3 = RZ with flush; an optional
+mode, not in the paper) every encoding with exponent field 0 reads as a zero
+of its sign, an exact result of magnitude below the smallest normal is a zero
+of its sign, and the search runs over the normal values only.
+
 Only practical for formats of up to about 12 bits.
 """
 from __future__ import annotations
@@ -21,7 +26,7 @@ import bisect
 from fractions import Fraction
 from functools import lru_cache
 
-RN, RZ = 0, 1
+RN, RZ, RN_FTZ, RZ_FTZ = 0, 1, 2, 3
 
 
 class Format:
@@ -40,6 +45,10 @@ class Format:
         self.ovf_rn = self.max_finite + top_ulp / 2
         self.nan = (self.emax << M) | (1 << (M - 1))
         self.sign_bit = 1 << (E + M)
+        self.min_normal = Fraction(2) ** (1 - self.bias)
+        # the normal encodings only (exponent field >= 1), for flush to zero
+        self.norm_codes = [c for c in self.pos_codes if c >> M]
+        self.norm_vals = [self.value(c) for c in self.norm_codes]
 
     # -- decoding ---------------------------------------------------------------
     def fields(self, code: int):
@@ -55,6 +64,12 @@ class Format:
         else:
             v = (1 + Fraction(f, 2 ** self.M)) * Fraction(2) ** (e - self.bias)
         return -v if s else v
+
+    def operand(self, code: int, rnd: int) -> Fraction:
+        """Value of a finite operand under the rounding mode's zero rule."""
+        if rnd & 2 and self.fields(code)[1] == 0:
+            return Fraction(0)
+        return self.value(code)
 
     def is_nan(self, code):
         _, e, f = self.fields(code)
@@ -74,28 +89,31 @@ class Format:
         s = 1 if v < 0 else 0
         a = -v if s else v
         sgn = s * self.sign_bit
-        if rnd == RN:
+        rz, ftz = rnd & 1, rnd & 2
+        if ftz and a < self.min_normal:
+            return sgn                            # tiny: a zero of the result's sign
+        if not rz:
             if a >= self.ovf_rn:
                 return self.inf(s)
         else:
             if a > self.max_finite:
                 return sgn | self.pos_codes[-1]
-        vals = self.pos_vals
+        codes, vals = (self.norm_codes, self.norm_vals) if ftz else (self.pos_codes, self.pos_vals)
         i = bisect.bisect_right(vals, a) - 1      # vals[i] <= a
         if vals[i] == a:
-            return sgn | self.pos_codes[i]
-        if rnd == RZ:
-            return sgn | self.pos_codes[i]
+            return sgn | codes[i]
+        if rz:
+            return sgn | codes[i]
         lo, hi = vals[i], vals[i + 1] if i + 1 < len(vals) else None
         if hi is None:                            # between max and the RN boundary
-            return sgn | self.pos_codes[i]
+            return sgn | codes[i]
         dl, dh = a - lo, hi - a
         if dl < dh:
-            return sgn | self.pos_codes[i]
+            return sgn | codes[i]
         if dh < dl:
-            return sgn | self.pos_codes[i + 1]
+            return sgn | codes[i + 1]
         # tie: the neighbour with an even encoding
-        return sgn | (self.pos_codes[i] if self.pos_codes[i] % 2 == 0 else self.pos_codes[i + 1])
+        return sgn | (codes[i] if codes[i] % 2 == 0 else codes[i + 1])
 
     # -- operations ---------------------------------------------------------------
     def add(self, x: int, y: int, rnd: int) -> int:
@@ -108,7 +126,7 @@ class Format:
             return self.inf(sx)
         if self.is_inf(y):
             return self.inf(sy)
-        v = self.value(x) + self.value(y)
+        v = self.operand(x, rnd) + self.operand(y, rnd)
         if v == 0:
             # exact zero: -0 only for (-0) + (-0); otherwise +0 (RN and RZ)
             return self.sign_bit if (sx and sy) else 0
@@ -124,10 +142,10 @@ class Format:
         s = sx ^ sy
         if self.is_inf(x) or self.is_inf(y):
             other = y if self.is_inf(x) else x
-            if not self.is_inf(other) and self.value(other) == 0:
+            if not self.is_inf(other) and self.operand(other, rnd) == 0:
                 return self.nan
             return self.inf(s)
-        v = self.value(x) * self.value(y)
+        v = self.operand(x, rnd) * self.operand(y, rnd)
         if v == 0:
             return s * self.sign_bit
         r = self.round(v, rnd)

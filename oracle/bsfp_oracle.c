@@ -20,6 +20,12 @@
  *   value, x+(-x) = +0, canonical NaN = sign 0, exponent all ones, fraction
  *   1<<(M-1)).
  *
+ *   Flush to zero (an optional mode, not in the paper): an operand with
+ *   exponent field 0 is read as a zero of its sign, and a nonzero exact result
+ *   whose magnitude is below the smallest normal 2^(1-bias) is a zero of its
+ *   sign (tininess judged on the exact value, before rounding); everything
+ *   else is rounded as above with M+1 significant bits.
+ *
  *   pack / unpack follow the bitslice layout of Sec. 2 (Fig. 1) and Sec. 4
  *   (Fig. 3): bit b of element i lives in bit (i mod 32) of word i/32 of slice
  *   b; slice 0 is the least significant bit of the encoding (the carry of the
@@ -121,13 +127,14 @@ static int big_bitlen(const big *a) {
 /* Format                                                                    */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int E, M, rz;          /* exponent bits, fraction bits, 1 = round toward zero */
+    int E, M, rz, ftz;     /* exponent bits, fraction bits, 1 = round toward zero, 1 = flush to zero */
     int bias, emax;        /* bias = 2^(E-1)-1, emax = 2^E-1 (all-ones field)      */
 } fmt_t;
 
-static fmt_t mkfmt(int E, int M, int rz) {
+/* mode: bit 0 = round toward zero (else to nearest even), bit 1 = flush to zero */
+static fmt_t mkfmt(int E, int M, int mode) {
     fmt_t f;
-    f.E = E; f.M = M; f.rz = rz;
+    f.E = E; f.M = M; f.rz = mode & 1; f.ftz = (mode >> 1) & 1;
     f.bias = (1 << (E - 1)) - 1;
     f.emax = (1 << E) - 1;
     return f;
@@ -154,8 +161,8 @@ static val_t decode(const fmt_t *f, uint32_t x) {
         return v;
     }
     v.cls = CLS_FINITE;
-    if (e == 0) {                       /* zero or subnormal */
-        v.mant = frac;
+    if (e == 0) {                       /* zero or subnormal (zero when flushing) */
+        v.mant = f->ftz ? 0 : frac;
         v.q = 1 - f->bias - f->M;
     } else {                            /* normal: implicit leading one */
         v.mant = ((uint64_t)1 << f->M) + frac;
@@ -186,6 +193,8 @@ static uint32_t round_encode(const fmt_t *f, int s, const big *T, int q) {
     int u = k - 1 + q;                     /* exponent of the leading bit */
     int qmin = 1 - f->bias - M;            /* weight of the smallest subnormal */
     int r;                                 /* number of low bits dropped */
+    if (f->ftz && u < 1 - f->bias)         /* tiny: a zero of the result's sign */
+        return enc(f, s, 0, 0);
     if (u >= 1 - f->bias) r = k - (M + 1); /* normal range: keep M+1 bits */
     else r = qmin - q;                     /* subnormal range: quantise to 2^qmin */
 
@@ -265,7 +274,8 @@ static uint32_t o_mul(const fmt_t *f, uint32_t x, uint32_t y) {
 static uint32_t flip_sign(const fmt_t *f, uint32_t y) { return y ^ (1u << (f->E + f->M)); }
 
 /* ------------------------------------------------------------------------ */
-/* Exported element-wise entry points (ctypes).  rz: 0 = RN-even, 1 = RZ.   */
+/* Exported element-wise entry points (ctypes).  rz: the rounding mode,     */
+/* 0 = RN-even, 1 = RZ, 2 = RN with flush to zero, 3 = RZ with flush.      */
 /* ------------------------------------------------------------------------ */
 uint32_t oracle_add1(int E, int M, int rz, uint32_t x, uint32_t y) { fmt_t f = mkfmt(E, M, rz); return o_add(&f, x, y); }
 uint32_t oracle_sub1(int E, int M, int rz, uint32_t x, uint32_t y) { fmt_t f = mkfmt(E, M, rz); return o_add(&f, x, flip_sign(&f, y)); }

@@ -15,7 +15,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbsfp.so")
 
-RN, RZ = 0, 1
+RN, RZ, RN_FTZ, RZ_FTZ = 0, 1, 2, 3
 OP_ADD, OP_SUB, OP_MUL, OP_FMA2 = 0, 1, 2, 3
 OPS = {"add": OP_ADD, "sub": OP_SUB, "mul": OP_MUL, "fma2": OP_FMA2}
 
@@ -46,7 +46,9 @@ class bsfp_format(ctypes.Structure):
         return 1 + self.exp_bits + self.man_bits
 
     def __repr__(self):
-        return "bsfp_format(1/%d/%d, %s)" % (self.exp_bits, self.man_bits, "RZ" if self.rnd else "RN")
+        return "bsfp_format(1/%d/%d, %s)" % (self.exp_bits, self.man_bits,
+                                             ("RN", "RZ", "RN_FTZ", "RZ_FTZ")[self.rnd] if 0 <= self.rnd < 4
+                                             else str(self.rnd))
 
 
 Format = bsfp_format

@@ -22,7 +22,7 @@
 
 namespace bsfp {
 
-BinopEntry g_binop_table[TAB_E][TAB_M][2][OPC_COUNT];
+BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_COUNT];
 
 /* Each exponent width is compiled as two translation units, M in [1, 11]
  * and [12, 23]; each fills its part of the table. */
@@ -51,8 +51,8 @@ struct Shape {
     int8_t wpt;
     int16_t bps;
 };
-static Shape g_shape[TAB_E][TAB_M][2][OPC_COUNT];
-static int g_occ[TAB_E][TAB_M][2][OPC_COUNT][5];   /* cached occupancy per wpt */
+static Shape g_shape[TAB_E][TAB_M][TAB_R][OPC_COUNT];
+static int g_occ[TAB_E][TAB_M][TAB_R][OPC_COUNT][5];   /* cached occupancy per wpt */
 static std::mutex g_shape_mu;
 
 static std::atomic<int64_t> g_launches{0};
@@ -65,7 +65,7 @@ static bsfp_status cuda_fail(cudaError_t e) {
 
 bool format_ok(const bsfp_format& f) {
     return f.exp_bits >= 2 && f.exp_bits <= 8 && f.man_bits >= 1 && f.man_bits <= 23 &&
-           1 + f.exp_bits + f.man_bits <= 32 && (f.rnd == BSFP_RN || f.rnd == BSFP_RZ);
+           1 + f.exp_bits + f.man_bits <= 32 && f.rnd >= BSFP_RN && f.rnd <= BSFP_RZ_FTZ;
 }
 
 static int bits_of(const bsfp_format& f) { return 1 + f.exp_bits + f.man_bits; }

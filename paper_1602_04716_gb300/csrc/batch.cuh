@@ -121,8 +121,10 @@ typedef cudaError_t (*batch_launch_fn)(const JobDesc* jobs, const int32_t* tile_
 batch_launch_fn batch_launcher(int opc, int wpt);
 const void* batch_kernel_ptr(int opc, int wpt);
 
-/* Kind of a format in the batched set, or -1. */
+/* Kind of a format in the batched set, or -1 (also for the flush-to-zero
+ * modes, which run as plain kernels). */
 inline int batch_kind(int E, int M, int rnd) {
+    if (rnd != 0 && rnd != 1) return -1;
     for (int i = 0; i < BATCH_NFMT; ++i)
         if (BATCH_E[i] == E && BATCH_M[i] == M) return 2 * i + (rnd ? 1 : 0);
     return -1;

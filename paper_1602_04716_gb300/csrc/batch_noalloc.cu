@@ -71,6 +71,7 @@ __device__ int dev_opclass(int op) {
 /* Kind of a format in the batched set (as batch_kind on the host), or -1. */
 template <int I = 0>
 __device__ int dev_kind(int E, int M, int rnd) {
+    if (rnd != 0 && rnd != 1) return -1;
     if constexpr (I == BATCH_NFMT) {
         return -1;
     } else {

@@ -74,26 +74,27 @@ __device__ __forceinline__ void vstore(uint32_t* p, const uint32_t* w) {
 /* The circuit for one word column.  OPC_ADDSUB takes the sign flip at run
  * time (one extra gate) so that add and sub share a kernel.  Formats with a
  * generated netlist (gen_circuit.cuh) run it; the others the templates. */
-template <int E, int M, bool RZ, int OPC>
+template <int E, int M, int R, int OPC>
 __device__ __forceinline__ void column_op(uint32_t* x, uint32_t* y, const uint32_t* z, uint32_t* r, uint32_t negb) {
     constexpr int B = 1 + E + M;
-    if constexpr (GenCircuit<E, M, RZ, OPC>::available) {
+    constexpr bool RZ = mode_rz(R), FTZ = mode_ftz(R);
+    if constexpr (GenCircuit<E, M, R, OPC>::available) {
         if constexpr (OPC == OPC_ADDSUB) y[B - 1] ^= negb;
-        GenCircuit<E, M, RZ, OPC>::eval(x, y, z, r);
+        GenCircuit<E, M, R, OPC>::eval(x, y, z, r);
     } else if constexpr (OPC == OPC_ADDSUB) {
         y[B - 1] ^= negb;
-        fp_add<E, M, RZ, false>(x, y, r);
+        fp_add<E, M, RZ, false, FTZ>(x, y, r);
     } else if constexpr (OPC == OPC_MUL) {
-        fp_mul<E, M, RZ>(x, y, r);
+        fp_mul<E, M, RZ, FTZ>(x, y, r);
     } else {
         uint32_t p[B];
-        fp_mul<E, M, RZ>(x, y, p);
-        fp_add<E, M, RZ, false>(p, z, r);
+        fp_mul<E, M, RZ, FTZ>(x, y, p);
+        fp_add<E, M, RZ, false, FTZ>(p, z, r);
     }
 }
 
 /* WPT word columns starting at w0 (a multiple of WPT). */
-template <int E, int M, bool RZ, int OPC, int WPT>
+template <int E, int M, int R, int OPC, int WPT>
 __device__ __forceinline__ void binop_chunk(const BinopArgs& p, int64_t w0) {
     constexpr int B = 1 + E + M;
     uint32_t xa[B][WPT], xb[B][WPT], xc[(OPC == OPC_FMA2) ? B : 1][WPT];
@@ -115,7 +116,7 @@ __device__ __forceinline__ void binop_chunk(const BinopArgs& p, int64_t w0) {
             y[i] = xb[i][k];
             z[i] = (OPC == OPC_FMA2) ? xc[(OPC == OPC_FMA2) ? i : 0][k] : 0u;
         }
-        column_op<E, M, RZ, OPC>(x, y, z, o, p.negb);
+        column_op<E, M, R, OPC>(x, y, z, o, p.negb);
 #pragma unroll
         for (int i = 0; i < B; ++i) r[i][k] = o[i];
     }
@@ -134,12 +135,12 @@ __device__ __forceinline__ void binop_chunk(const BinopArgs& p, int64_t w0) {
     for (int i = 0; i < B; ++i) vstore<WPT>(p.out + i * p.S + w0, r[i]);
 }
 
-template <int E, int M, bool RZ, int OPC, int WPT>
+template <int E, int M, int R, int OPC, int WPT>
 __global__ void __launch_bounds__(128) binop_kernel(const BinopArgs p) {
     const int64_t nchunks = p.S / WPT;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += stride)
-        binop_chunk<E, M, RZ, OPC, WPT>(p, ch * WPT);
+        binop_chunk<E, M, R, OPC, WPT>(p, ch * WPT);
 }
 
 /* Words-per-thread variants compiled per (format, op class).  Every format
@@ -158,7 +159,8 @@ constexpr unsigned wpt_mask(int E, int M, int opc) {
     return 1u | (in * 2 <= 128 ? 2u : 0u) | (in * 4 <= 128 ? 4u : 0u);
 }
 
-/* Host side: one launcher per (E, M, RZ, OPC), covering the WPT variants. */
+/* Host side: one launcher per (E, M, rounding mode R, OPC), covering the WPT
+ * variants. */
 typedef cudaError_t (*binop_launch_fn)(const BinopArgs& p, int wpt, int grid, cudaStream_t s);
 typedef const void* (*binop_kernel_fn)(int wpt);
 
@@ -169,39 +171,39 @@ struct BinopEntry {
     int default_wpt;
 };
 
-template <int E, int M, bool RZ, int OPC>
+template <int E, int M, int R, int OPC>
 cudaError_t binop_launch(const BinopArgs& p, int wpt, int grid, cudaStream_t s) {
     constexpr unsigned mask = wpt_mask(E, M, OPC);
     if (wpt == 1 && (mask & 1u)) {
-        if constexpr ((mask & 1u) != 0) binop_kernel<E, M, RZ, OPC, 1><<<grid, 128, 0, s>>>(p);
+        if constexpr ((mask & 1u) != 0) binop_kernel<E, M, R, OPC, 1><<<grid, 128, 0, s>>>(p);
     } else if (wpt == 2 && (mask & 2u)) {
-        if constexpr ((mask & 2u) != 0) binop_kernel<E, M, RZ, OPC, 2><<<grid, 128, 0, s>>>(p);
+        if constexpr ((mask & 2u) != 0) binop_kernel<E, M, R, OPC, 2><<<grid, 128, 0, s>>>(p);
     } else if (wpt == 4 && (mask & 4u)) {
-        if constexpr ((mask & 4u) != 0) binop_kernel<E, M, RZ, OPC, 4><<<grid, 128, 0, s>>>(p);
+        if constexpr ((mask & 4u) != 0) binop_kernel<E, M, R, OPC, 4><<<grid, 128, 0, s>>>(p);
     } else {
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <int E, int M, bool RZ, int OPC>
+template <int E, int M, int R, int OPC>
 const void* binop_kernel_ptr(int wpt) {
     constexpr unsigned mask = wpt_mask(E, M, OPC);
-    if constexpr ((mask & 1u) != 0) if (wpt == 1) return (const void*)binop_kernel<E, M, RZ, OPC, 1>;
-    if constexpr ((mask & 2u) != 0) if (wpt == 2) return (const void*)binop_kernel<E, M, RZ, OPC, 2>;
-    if constexpr ((mask & 4u) != 0) if (wpt == 4) return (const void*)binop_kernel<E, M, RZ, OPC, 4>;
+    if constexpr ((mask & 1u) != 0) if (wpt == 1) return (const void*)binop_kernel<E, M, R, OPC, 1>;
+    if constexpr ((mask & 2u) != 0) if (wpt == 2) return (const void*)binop_kernel<E, M, R, OPC, 2>;
+    if constexpr ((mask & 4u) != 0) if (wpt == 4) return (const void*)binop_kernel<E, M, R, OPC, 4>;
     return nullptr;
 }
 
-template <int E, int M, bool RZ, int OPC>
+template <int E, int M, int R, int OPC>
 constexpr BinopEntry make_entry() {
-    return BinopEntry{binop_launch<E, M, RZ, OPC>, binop_kernel_ptr<E, M, RZ, OPC>, wpt_mask(E, M, OPC),
+    return BinopEntry{binop_launch<E, M, R, OPC>, binop_kernel_ptr<E, M, R, OPC>, wpt_mask(E, M, OPC),
                       (wpt_mask(E, M, OPC) & 2u) ? 2 : 1};
 }
 
 /* Table of every compiled (E, M, rounding, op class); filled by the
  * per-exponent translation units. */
-constexpr int TAB_E = 9, TAB_M = 24;
-extern BinopEntry g_binop_table[TAB_E][TAB_M][2][OPC_COUNT];
+constexpr int TAB_E = 9, TAB_M = 24, TAB_R = 4;
+extern BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_COUNT];
 
 }  // namespace bsfp

@@ -2,8 +2,9 @@
  * binop_inst.cu -- instantiates the element-wise kernels for one exponent
  * width.  The build compiles this file once per E in [2, 8] with -DBSFP_E=E,
  * so the 7 translation units build in parallel; each fills its slice of the
- * dispatch table for M in [BSFP_M_LO, BSFP_M_HI], both rounding modes and the
- * three kernel classes (add/sub, mul, fma2).  This replaces the paper's
+ * dispatch table for M in [BSFP_M_LO, BSFP_M_HI], both rounding modes (and
+ * their flush-to-zero forms for the tuned formats) and the three kernel
+ * classes (add/sub, mul, fma2).  This replaces the paper's
  * library generator (Sec. 5.1), which emitted code per configured format.
  */
 #include "binop.cuh"
@@ -20,15 +21,23 @@
 
 namespace bsfp {
 
+template <int E, int M, int R>
+static void fill_mode() {
+    g_binop_table[E][M][R][OPC_ADDSUB] = make_entry<E, M, R, OPC_ADDSUB>();
+    g_binop_table[E][M][R][OPC_MUL] = make_entry<E, M, R, OPC_MUL>();
+    g_binop_table[E][M][R][OPC_FMA2] = make_entry<E, M, R, OPC_FMA2>();
+}
+
 template <int E, int M>
 static void fill_format() {
     if constexpr (M >= BSFP_M_LO && M <= BSFP_M_HI && 1 + E + M <= 32) {
-        g_binop_table[E][M][0][OPC_ADDSUB] = make_entry<E, M, false, OPC_ADDSUB>();
-        g_binop_table[E][M][1][OPC_ADDSUB] = make_entry<E, M, true, OPC_ADDSUB>();
-        g_binop_table[E][M][0][OPC_MUL] = make_entry<E, M, false, OPC_MUL>();
-        g_binop_table[E][M][1][OPC_MUL] = make_entry<E, M, true, OPC_MUL>();
-        g_binop_table[E][M][0][OPC_FMA2] = make_entry<E, M, false, OPC_FMA2>();
-        g_binop_table[E][M][1][OPC_FMA2] = make_entry<E, M, true, OPC_FMA2>();
+        fill_mode<E, M, 0>();   /* RN */
+        fill_mode<E, M, 1>();   /* RZ */
+        /* the flush-to-zero modes are compiled for the tuned formats only */
+        if constexpr (tuned_format(E, M)) {
+            fill_mode<E, M, 2>();
+            fill_mode<E, M, 3>();
+        }
     }
     if constexpr (M < BSFP_M_HI) fill_format<E, M + 1>();
 }

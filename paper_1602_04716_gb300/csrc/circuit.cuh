@@ -231,9 +231,15 @@ template <int M, int ND, class W> BSFP_HD void assemble(const W* D, const W* sig
  * the normaliser cannot always shift a zero significand all the way down);
  * sgn: sign of the result unless zs (an exact zero that is +0).  RN overflows
  * to Inf, RZ to max finite. */
-template <int E, int M, int NF, bool RZ, class W>
-BSFP_HD void encode(const W* mag, W spec, W nan, W zero, W sgn, W zs, W* r) {
+template <int E, int M, int NF, bool RZ, class W, bool FTZ = false>
+BSFP_HD void encode(const W* mag_in, W spec, W nan, W zero, W sgn, W zs, W* r) {
     constexpr int B = 1 + E + M;
+    /* with flush to zero a zero result may carry a nonzero significand (a
+     * flushed tiny value): its fraction is cleared here */
+    W mf[M + NF];
+    BSFP_UNROLL
+    for (int i = 0; i < M + NF; ++i) mf[i] = (FTZ && i < M) ? ANDN(mag_in[i], zero) : mag_in[i];
+    const W* mag = mf;
     W ovf = and_n<E>(mag + M);
     if constexpr (NF > E) ovf = OR(ovf, or_n<NF - E>(mag + M + E));
     if constexpr (!RZ) {
@@ -260,11 +266,30 @@ BSFP_HD void encode(const W* mag, W spec, W nan, W zero, W sgn, W zs, W* r) {
 
 /* -------------------------------------------------------------- add/sub --- */
 /* r = a + b (NEG_B: a - b), one rounding (Sec. 4, Table 1, Add/Sub). */
-template <int E, int M, bool RZ, bool NEG_B, class W>
+template <int E, int M, bool RZ, bool NEG_B, bool FTZ = false, class W>
 BSFP_HD void fp_add(const W* a, const W* b, W* r) {
     static_assert(E >= 2 && M >= 1 && 1 + E + M <= 32, "format out of range");
     constexpr int B = 1 + E + M;
     constexpr int NM = E + M;   /* magnitude bits */
+    if constexpr (FTZ) {
+        /* flush to zero: an operand with exponent field 0 is a zero of its
+         * sign (its fraction is cleared); the sum of two such operands is
+         * exact, so a tiny result is exactly a subnormal of the gradual-
+         * underflow adder, and flushing it after the adder (fraction cleared
+         * when the exponent field is 0) keeps the result's sign */
+        W x[B], y[B];
+        const W nza = or_n<E>(a + M), nzb = or_n<E>(b + M);
+        BSFP_UNROLL
+        for (int i = 0; i < B; ++i) {
+            x[i] = i < M ? AND(a[i], nza) : a[i];
+            y[i] = i < M ? AND(b[i], nzb) : b[i];
+        }
+        fp_add<E, M, RZ, NEG_B, false>(x, y, r);
+        const W nzr = or_n<E>(r + M);
+        BSFP_UNROLL
+        for (int i = 0; i < M; ++i) r[i] = AND(r[i], nzr);
+        return;
+    }
     const W sa = a[B - 1];
     const W sb = NEG_B ? NOT(b[B - 1]) : b[B - 1];
 
@@ -392,9 +417,93 @@ template <int n, class W> BSFP_HD void umul(const W* A, const W* Bv, W* P) {
     P[2 * n - 1] = c;
 }
 
+/* r = a * b with flush to zero: operands with exponent field 0 are zeros of
+ * their sign, and a product whose exact magnitude is below the smallest
+ * normal (tiny before rounding) is a zero of the product's sign.  Both
+ * significands are then normal, the product lies in [1, 4) and needs a
+ * one-position normalisation only: neither the leading-zero normaliser nor
+ * the right shifter into the subnormal range of the gradual-underflow
+ * multiplier is needed -- the gates the paper saves with a flush mode. */
+template <int E, int M, bool RZ, class W> BSFP_HD void fp_mul_ftz(const W* a, const W* b, W* r) {
+    constexpr int B = 1 + E + M;
+    constexpr int N1 = M + 1;
+    constexpr int NP = 2 * M + 2;
+    constexpr int NU = E + 2;
+    const W s = XOR(a[B - 1], b[B - 1]);
+    const W* ea = a + M;
+    const W* eb = b + M;
+    const W nzA = or_n<E>(ea);
+    const W nzB = or_n<E>(eb);
+
+    /* significand product of 1.fa and 1.fb */
+    W SA[N1], SB[N1];
+    BSFP_UNROLL
+    for (int i = 0; i < M; ++i) {
+        SA[i] = a[i];
+        SB[i] = b[i];
+    }
+    SA[M] = ~W(0u);
+    SB[M] = ~W(0u);
+    W P[NP];
+    umul<N1>(SA, SB, P);
+    const W top = P[NP - 1];
+
+    /* D = ea + eb - bias - 1 + top in NU-bit two's complement (the exponent
+     * field of the result is D + 1, the leading one being added by assemble):
+     * a carry-save step of ea, eb and the constant -(bias + 1) = -2^(E-1),
+     * then a ripple adder with top as carry-in */
+    constexpr uint32_t KB = ((uint32_t)(-(1 << (E - 1)))) & ((1u << NU) - 1u);
+    W D[NU];
+    {
+        W cs[NU], cc[NU + 1];
+        cc[0] = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            const W ai = (i < E) ? ea[(i < E) ? i : 0] : W(0u);
+            const W bi = (i < E) ? eb[(i < E) ? i : 0] : W(0u);
+            const bool k = (KB >> i) & 1u;
+            cs[i] = k ? NOT(XOR(ai, bi)) : XOR(ai, bi);
+            cc[i + 1] = k ? OR(ai, bi) : AND(ai, bi);
+        }
+        W c = top;
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            D[i] = XOR3(cs[i], cc[i], c);
+            if (i + 1 < NU) c = MAJ(cs[i], cc[i], c);
+        }
+    }
+    const W tiny = D[NU - 1];        /* D < 0: exponent field < 1 */
+
+    /* one-position normalisation, guard and sticky */
+    W sig[N1];
+    BSFP_UNROLL
+    for (int i = 0; i < N1; ++i) sig[i] = MUX(top, P[M + 1 + i], P[M + i]);
+    W rup = W(0u);
+    if constexpr (!RZ) {
+        const W g = MUX(top, P[M], P[M - 1 >= 0 ? M - 1 : 0]);
+        const W st0 = or_n<M - 1>(P);                 /* below the guard when top = 0 */
+        const W st = (M >= 1) ? ANDOR(top, P[M - 1], st0) : st0;
+        rup = F3<LUT_G_AND_LS>(g, sig[0], st);
+    }
+    W mag[M + NU];
+    assemble<M, NU - 1>(D, sig, rup, mag);
+
+    /* specials: NaN for NaN operands and 0 * Inf (zeros include flushed
+     * operands); Inf otherwise */
+    const W aspec = and_n<E>(ea), bspec = and_n<E>(eb);
+    const W fA = or_n<M>(a), fB = or_n<M>(b);
+    const W nan = OR(F3<LUT_AND_OR_NOT>(aspec, fA, nzB), F3<LUT_AND_OR_NOT>(bspec, fB, nzA));
+    const W zero = OR(NOT(AND(nzA, nzB)), tiny);
+    encode<E, M, NU, RZ, W, true>(mag, OR(aspec, bspec), nan, zero, s, W(0u), r);
+}
+
 /* r = a * b, one rounding (Sec. 4, Table 1, Mul). */
-template <int E, int M, bool RZ, class W> BSFP_HD void fp_mul(const W* a, const W* b, W* r) {
+template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void fp_mul(const W* a, const W* b, W* r) {
     static_assert(E >= 2 && M >= 1 && 1 + E + M <= 32, "format out of range");
+    if constexpr (FTZ) {
+        fp_mul_ftz<E, M, RZ>(a, b, r);
+        return;
+    }
     constexpr int B = 1 + E + M;
     constexpr int N1 = M + 1;         /* significand bits */
     constexpr int NP = 2 * M + 2;     /* product bits */
@@ -508,19 +617,26 @@ template <int E, int M, bool RZ, class W> BSFP_HD void fp_mul(const W* a, const 
 /* ----------------------------------------------------------------- ops --- */
 enum Op : int { OP_ADD = 0, OP_SUB = 1, OP_MUL = 2, OP_FMA2 = 3 };
 
+/* Rounding mode of a format: bit 0 = toward zero (else to nearest even),
+ * bit 1 = flush to zero (operands and results below the normal range are
+ * zeros of their sign). */
+BSFP_HDC constexpr bool mode_rz(int R) { return (R & 1) != 0; }
+BSFP_HDC constexpr bool mode_ftz(int R) { return (R & 2) != 0; }
+
 /* r = op(a, b[, c]); fma2 = add(mul(a, b), c), each rounded. */
-template <int E, int M, bool RZ, int OP, class W>
+template <int E, int M, int R, int OP, class W>
 BSFP_HD void fp_op(const W* a, const W* b, const W* c, W* r) {
+    constexpr bool RZ = mode_rz(R), FTZ = mode_ftz(R);
     if constexpr (OP == OP_ADD) {
-        fp_add<E, M, RZ, false>(a, b, r);
+        fp_add<E, M, RZ, false, FTZ>(a, b, r);
     } else if constexpr (OP == OP_SUB) {
-        fp_add<E, M, RZ, true>(a, b, r);
+        fp_add<E, M, RZ, true, FTZ>(a, b, r);
     } else if constexpr (OP == OP_MUL) {
-        fp_mul<E, M, RZ>(a, b, r);
+        fp_mul<E, M, RZ, FTZ>(a, b, r);
     } else {
         W p[1 + E + M];
-        fp_mul<E, M, RZ>(a, b, p);
-        fp_add<E, M, RZ, false>(p, c, r);
+        fp_mul<E, M, RZ, FTZ>(a, b, p);
+        fp_add<E, M, RZ, false, FTZ>(p, c, r);
     }
 }
 

@@ -16,7 +16,8 @@
  *
  * Usage: circuitgen OUT.cuh    (formats from -DBSFP_GEN_FORMATS="X(E, M) ...")
  *
- * For each format and rounding it prints GenCircuit<E, M, RZ, OPC>
+ * For each format and rounding mode R (bit 0 toward zero, bit 1 flush to
+ * zero) it prints GenCircuit<E, M, R, OPC>
  * specialisations for the op classes add (b's sign flip is applied by the
  * caller), mul and fma2, with eval(a, b, c, r) over the B slices of each
  * operand.  The printed file is included inside namespace bsfp by
@@ -54,16 +55,16 @@ std::string value_name(int32_t ref, int B) {
     return inv ? "~" + s : s;
 }
 
-template <int E, int M, bool RZ, int OP>
+template <int E, int M, int R, int OP>
 void emit(FILE* f, int opc) {
     constexpr int B = 1 + E + M;
     Graph g;
     GW r[B];
-    record<E, M, RZ, OP>(g, r);
+    record<E, M, R, OP>(g, r);
     const std::vector<char> live = live_set(g, r, B);
     long n = 0;
     for (char m : live) n += m;
-    fprintf(f, "template <> struct GenCircuit<%d, %d, %s, %d> {\n", E, M, RZ ? "true" : "false", opc);
+    fprintf(f, "template <> struct GenCircuit<%d, %d, %d, %d> {\n", E, M, R, opc);
     fprintf(f, "    static constexpr bool available = true;\n");
     fprintf(f, "    static constexpr int gates = %ld;\n", n);
     fprintf(f, "    BSFP_GEN_FN static void eval(const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* r) {\n");
@@ -84,15 +85,21 @@ void emit(FILE* f, int opc) {
     fprintf(f, "    }\n};\n");
 }
 
+template <int E, int M, int R>
+void emit_mode(FILE* f) {
+    /* op classes: 0 = add/sub, 1 = mul, 2 = fma2 (OpClass of binop.cuh) */
+    emit<E, M, R, OP_ADD>(f, 0);
+    emit<E, M, R, OP_MUL>(f, 1);
+    emit<E, M, R, OP_FMA2>(f, 2);
+}
+
+/* every rounding mode: RN, RZ, and both with flush to zero */
 template <int E, int M>
 void emit_format(FILE* f) {
-    /* op classes: 0 = add/sub, 1 = mul, 2 = fma2 (OpClass of binop.cuh) */
-    emit<E, M, false, OP_ADD>(f, 0);
-    emit<E, M, true, OP_ADD>(f, 0);
-    emit<E, M, false, OP_MUL>(f, 1);
-    emit<E, M, true, OP_MUL>(f, 1);
-    emit<E, M, false, OP_FMA2>(f, 2);
-    emit<E, M, true, OP_FMA2>(f, 2);
+    emit_mode<E, M, 0>(f);
+    emit_mode<E, M, 1>(f);
+    emit_mode<E, M, 2>(f);
+    emit_mode<E, M, 3>(f);
 }
 
 }  // namespace

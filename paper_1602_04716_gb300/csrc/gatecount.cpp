@@ -18,35 +18,42 @@ namespace bsfp {
 namespace gc {
 namespace {
 
-template <int E, int M, bool RZ, int OP> static long count_one() {
+template <int E, int M, int R, int OP> static long count_one() {
     constexpr int B = 1 + E + M;
     Graph g;
     GW r[B];
-    record<E, M, RZ, OP>(g, r);
+    record<E, M, R, OP>(g, r);
     return count_live(g, r, B);
 }
 
-template <int E, int M> static long count_fmt(int rz, int op) {
+template <int E, int M, int OP> static long count_op(int rnd) {
+    switch (rnd) {
+        case 0: return count_one<E, M, 0, OP>();
+        case 1: return count_one<E, M, 1, OP>();
+        case 2: return count_one<E, M, 2, OP>();
+        case 3: return count_one<E, M, 3, OP>();
+    }
+    return -1;
+}
+
+/* rnd: rounding mode (bit 0 toward zero, bit 1 flush to zero) */
+template <int E, int M> static long count_fmt(int rnd, int op) {
     if constexpr (E + M + 1 > 32) {
         return -1;
     } else {
-        switch (op * 2 + (rz ? 1 : 0)) {
-            case 0: return count_one<E, M, false, OP_ADD>();
-            case 1: return count_one<E, M, true, OP_ADD>();
-            case 2: return count_one<E, M, false, OP_SUB>();
-            case 3: return count_one<E, M, true, OP_SUB>();
-            case 4: return count_one<E, M, false, OP_MUL>();
-            case 5: return count_one<E, M, true, OP_MUL>();
-            case 6: return count_one<E, M, false, OP_FMA2>();
-            case 7: return count_one<E, M, true, OP_FMA2>();
+        switch (op) {
+            case 0: return count_op<E, M, OP_ADD>(rnd);
+            case 1: return count_op<E, M, OP_SUB>(rnd);
+            case 2: return count_op<E, M, OP_MUL>(rnd);
+            case 3: return count_op<E, M, OP_FMA2>(rnd);
         }
         return -1;
     }
 }
 
-template <int E, int M> static long count_m(int m, int rz, int op) {
-    if (m == M) return count_fmt<E, M>(rz, op);
-    if constexpr (M < 23) return count_m<E, M + 1>(m, rz, op);
+template <int E, int M> static long count_m(int m, int rnd, int op) {
+    if (m == M) return count_fmt<E, M>(rnd, op);
+    if constexpr (M < 23) return count_m<E, M + 1>(m, rnd, op);
     return -1;
 }
 
@@ -63,6 +70,6 @@ template <int E, int M> static long count_m(int m, int rz, int op) {
 #define BSFP_GC_CAT(a, b) BSFP_GC_CAT2(a, b)
 
 extern "C" long BSFP_GC_CAT(bsfp_gate_count_e, BSFP_E)(int man_bits, int rnd, int op) {
-    if (man_bits < 1 || man_bits > 23 || op < 0 || op > 3 || rnd < 0 || rnd > 1) return -1;
+    if (man_bits < 1 || man_bits > 23 || op < 0 || op > 3 || rnd < 0 || rnd > 3) return -1;
     return bsfp::gc::count_m<BSFP_E, 1>(man_bits, rnd, op);
 }

@@ -1,8 +1,9 @@
 /*
  * gen_circuit.cuh -- circuits printed gate by gate from their netlists.
  *
- * GenCircuit<E, M, RZ, OPC>::eval(a, b, c, r) computes the same function as
- * the circuit.cuh template for that format, rounding and op class, with one
+ * GenCircuit<E, M, R, OPC>::eval(a, b, c, r) computes the same function as
+ * the circuit.cuh template for that format, rounding mode R (bit 0 toward
+ * zero, bit 1 flush to zero) and op class, with one
  * 3-input logic instruction (LOP3, truth table as immediate) per gate of the
  * recorded netlist, so the instruction count is exactly the gate count G.
  * The specialisations come from gen_circuits.cuh, which circuitgen writes at
@@ -18,7 +19,7 @@
 
 namespace bsfp {
 
-template <int E, int M, bool RZ, int OPC>
+template <int E, int M, int R, int OPC>
 struct GenCircuit {
     static constexpr bool available = false;
 };

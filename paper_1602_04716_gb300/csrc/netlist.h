@@ -197,9 +197,10 @@ static long count_live(const Graph& g, const GW* out, int nout) {
     return n;
 }
 
-/* Record fp_op<E, M, RZ, OP> over inputs a = ids 1..B, b = B+1..2B,
- * c = 2B+1..3B into g; the B output refs go to r. */
-template <int E, int M, bool RZ, int OP> static void record(Graph& g, GW* r) {
+/* Record fp_op<E, M, R, OP> (R: rounding mode, bit 0 toward zero, bit 1
+ * flush to zero) over inputs a = ids 1..B, b = B+1..2B, c = 2B+1..3B into
+ * g; the B output refs go to r. */
+template <int E, int M, int R, int OP> static void record(Graph& g, GW* r) {
     constexpr int B = 1 + E + M;
     g.ninputs = 3 * B;
     g_graph = &g;
@@ -209,7 +210,7 @@ template <int E, int M, bool RZ, int OP> static void record(Graph& g, GW* r) {
         b[i] = GW((1 + B + i) << 1, 0);
         c[i] = GW((1 + 2 * B + i) << 1, 0);
     }
-    fp_op<E, M, RZ, OP>(a, b, c, r);
+    fp_op<E, M, R, OP>(a, b, c, r);
     g_graph = nullptr;
 }
 

@@ -9,7 +9,7 @@
 
 using namespace bsfp;
 
-template <int E, int M, bool RZ, int OP>
+template <int E, int M, int R, int OP>
 static void run(const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out, long nwords, long S) {
     constexpr int B = 1 + E + M;
     for (long w = 0; w < nwords; ++w) {
@@ -19,31 +19,40 @@ static void run(const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_
             y[i] = b[i * S + w];
             z[i] = c[i * S + w];
         }
-        fp_op<E, M, RZ, OP>(x, y, z, r);
+        fp_op<E, M, R, OP>(x, y, z, r);
         for (int i = 0; i < B; ++i) out[i * S + w] = r[i];
     }
 }
 
+template <int E, int M, int OP>
+static int dispatch_mode(int rnd, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out, long nwords,
+                         long S) {
+    switch (rnd) {
+        case 0: run<E, M, 0, OP>(a, b, c, out, nwords, S); return 0;
+        case 1: run<E, M, 1, OP>(a, b, c, out, nwords, S); return 0;
+        case 2: run<E, M, 2, OP>(a, b, c, out, nwords, S); return 0;
+        case 3: run<E, M, 3, OP>(a, b, c, out, nwords, S); return 0;
+    }
+    return -1;
+}
+
+/* rnd: rounding mode (bit 0 toward zero, bit 1 flush to zero) */
 template <int E, int M>
-static int dispatch_fmt(int rz, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
+static int dispatch_fmt(int rnd, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
                         long nwords, long S) {
-    switch (op * 2 + (rz ? 1 : 0)) {
-        case 0: run<E, M, false, OP_ADD>(a, b, c, out, nwords, S); return 0;
-        case 1: run<E, M, true, OP_ADD>(a, b, c, out, nwords, S); return 0;
-        case 2: run<E, M, false, OP_SUB>(a, b, c, out, nwords, S); return 0;
-        case 3: run<E, M, true, OP_SUB>(a, b, c, out, nwords, S); return 0;
-        case 4: run<E, M, false, OP_MUL>(a, b, c, out, nwords, S); return 0;
-        case 5: run<E, M, true, OP_MUL>(a, b, c, out, nwords, S); return 0;
-        case 6: run<E, M, false, OP_FMA2>(a, b, c, out, nwords, S); return 0;
-        case 7: run<E, M, true, OP_FMA2>(a, b, c, out, nwords, S); return 0;
+    switch (op) {
+        case 0: return dispatch_mode<E, M, OP_ADD>(rnd, a, b, c, out, nwords, S);
+        case 1: return dispatch_mode<E, M, OP_SUB>(rnd, a, b, c, out, nwords, S);
+        case 2: return dispatch_mode<E, M, OP_MUL>(rnd, a, b, c, out, nwords, S);
+        case 3: return dispatch_mode<E, M, OP_FMA2>(rnd, a, b, c, out, nwords, S);
     }
     return -1;
 }
 
 #define FMT(E, M) \
-    if (e == E && m == M) return dispatch_fmt<E, M>(rz, op, a, b, c, out, nwords, S);
+    if (e == E && m == M) return dispatch_fmt<E, M>(rnd, op, a, b, c, out, nwords, S);
 
-extern "C" int host_circuit(int e, int m, int rz, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+extern "C" int host_circuit(int e, int m, int rnd, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
                             uint32_t* out, long nwords, long S) {
     /* the formats the CPU tests exercise */
     FMT(2, 1) FMT(2, 3) FMT(3, 2) FMT(3, 3) FMT(2, 5) FMT(3, 4) FMT(4, 3) FMT(5, 2) FMT(4, 4) FMT(5, 4)

@@ -10,11 +10,11 @@
 
 using namespace bsfp;
 
-template <int E, int M, bool RZ, int OPC>
+template <int E, int M, int R, int OPC>
 static int run(bool neg_b, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out, long nwords,
                long S) {
     constexpr int B = 1 + E + M;
-    if constexpr (!GenCircuit<E, M, RZ, OPC>::available) {
+    if constexpr (!GenCircuit<E, M, R, OPC>::available) {
         return -1;
     } else {
         for (long w = 0; w < nwords; ++w) {
@@ -25,33 +25,43 @@ static int run(bool neg_b, const uint32_t* a, const uint32_t* b, const uint32_t*
                 z[i] = c[i * S + w];
             }
             if (neg_b) y[B - 1] = ~y[B - 1];
-            GenCircuit<E, M, RZ, OPC>::eval(x, y, z, r);
+            GenCircuit<E, M, R, OPC>::eval(x, y, z, r);
             for (int i = 0; i < B; ++i) out[i * S + w] = r[i];
         }
         return 0;
     }
 }
 
-template <int E, int M>
-static int dispatch_fmt(int rz, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
-                        long nwords, long S) {
+template <int E, int M, int R>
+static int dispatch_opc(int op, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out, long nwords,
+                        long S) {
     /* op: 0 add, 1 sub, 2 mul, 3 fma2 -> op classes 0 (add/sub), 1, 2 */
-    const bool neg = op == 1;
-    switch ((op == 0 || op == 1 ? 0 : op - 1) * 2 + (rz ? 1 : 0)) {
-        case 0: return run<E, M, false, 0>(neg, a, b, c, out, nwords, S);
-        case 1: return run<E, M, true, 0>(neg, a, b, c, out, nwords, S);
-        case 2: return run<E, M, false, 1>(neg, a, b, c, out, nwords, S);
-        case 3: return run<E, M, true, 1>(neg, a, b, c, out, nwords, S);
-        case 4: return run<E, M, false, 2>(neg, a, b, c, out, nwords, S);
-        case 5: return run<E, M, true, 2>(neg, a, b, c, out, nwords, S);
+    switch (op) {
+        case 0: return run<E, M, R, 0>(false, a, b, c, out, nwords, S);
+        case 1: return run<E, M, R, 0>(true, a, b, c, out, nwords, S);
+        case 2: return run<E, M, R, 1>(false, a, b, c, out, nwords, S);
+        case 3: return run<E, M, R, 2>(false, a, b, c, out, nwords, S);
+    }
+    return -1;
+}
+
+/* rnd: rounding mode (bit 0 toward zero, bit 1 flush to zero) */
+template <int E, int M>
+static int dispatch_fmt(int rnd, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
+                        long nwords, long S) {
+    switch (rnd) {
+        case 0: return dispatch_opc<E, M, 0>(op, a, b, c, out, nwords, S);
+        case 1: return dispatch_opc<E, M, 1>(op, a, b, c, out, nwords, S);
+        case 2: return dispatch_opc<E, M, 2>(op, a, b, c, out, nwords, S);
+        case 3: return dispatch_opc<E, M, 3>(op, a, b, c, out, nwords, S);
     }
     return -1;
 }
 
 #define FMT(E, M) \
-    if (e == E && m == M) return dispatch_fmt<E, M>(rz, op, a, b, c, out, nwords, S);
+    if (e == E && m == M) return dispatch_fmt<E, M>(rnd, op, a, b, c, out, nwords, S);
 
-extern "C" int host_gen_circuit(int e, int m, int rz, int op, const uint32_t* a, const uint32_t* b,
+extern "C" int host_gen_circuit(int e, int m, int rnd, int op, const uint32_t* a, const uint32_t* b,
                                 const uint32_t* c, uint32_t* out, long nwords, long S) {
     FMT(4, 3) FMT(4, 4) FMT(5, 7) FMT(5, 10) FMT(8, 7) FMT(8, 23)
     return -1;

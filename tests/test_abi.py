@@ -49,7 +49,7 @@ def test_plane_stride_and_sizes():
     assert bs.bsfp_container_bytes(bs.Format(9, 7)) == -1
 
 
-@pytest.mark.parametrize("fmt", [(1, 3, 0), (9, 3, 0), (4, 0, 0), (4, 24, 0), (4, 3, 2), (4, 3, -1)])
+@pytest.mark.parametrize("fmt", [(1, 3, 0), (9, 3, 0), (4, 0, 0), (4, 24, 0), (4, 3, 4), (4, 3, -1)])
 def test_bad_format_rejected(fmt):
     f = bs.Format(*fmt)
     L = _binding._lib()
@@ -158,3 +158,14 @@ def test_pipeline_arguments_validated_before_any_cuda_call():
     outs = (ctypes.c_void_p * 1)(256)
     assert L.bsfp_pipeline_run(None, bs.Format(4, 3), 1, ops, 256, 256, None, outs, 10) == bs.ERR_NULL
     L.bsfp_pipeline_free(None)
+
+
+def test_flush_to_zero_only_for_the_compiled_formats():
+    """RN/RZ with flush to zero (modes 2, 3) have kernels for the tuned
+    formats only; any other format is refused before anything runs."""
+    L = _binding._lib()
+    for rnd in (bs.RN_FTZ, bs.RZ_FTZ):
+        assert L.bsfp_add(bs.Format(6, 9, rnd), 256, 256, 256, 10, None) == bs.ERR_UNSUPPORTED
+        assert L.bsfp_variants_compiled(bs.Format(6, 9, rnd), 2) == 0
+        assert L.bsfp_variants_compiled(bs.Format(5, 7, rnd), 2) > 0
+        assert bs.bsfp_gate_count(bs.Format(5, 7, rnd), "mul") < bs.bsfp_gate_count(bs.Format(5, 7, rnd & 1), "mul")

@@ -83,9 +83,12 @@ def _first_bad(got, want, *ins):
 SMALL = [(2, 1), (2, 3), (3, 2), (3, 3), (2, 5), (3, 4), (4, 3), (5, 2)]
 
 
+MODES = [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ]
+
+
 @pytest.mark.parametrize("E,M", SMALL)
 @pytest.mark.parametrize("op", ["add", "sub", "mul"])
-@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+@pytest.mark.parametrize("rnd", MODES)
 def test_circuit_exhaustive_small(E, M, op, rnd):
     a, b = synth.all_pairs(1 + E + M)
     a, b = a.astype(np.uint32), b.astype(np.uint32)
@@ -94,7 +97,7 @@ def test_circuit_exhaustive_small(E, M, op, rnd):
     assert (got == want).all(), _first_bad(got, want, a, b)
 
 
-@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+@pytest.mark.parametrize("rnd", MODES)
 def test_circuit_fma2_1_4_3_sampled(rnd):
     n = 1 << 18
     a = synth.uniform_bits(8, n, 11).astype(np.uint32)
@@ -110,7 +113,7 @@ WIDE = [(4, 4), (5, 4), (4, 5), (5, 7), (5, 10), (8, 7), (8, 23), (3, 23), (8, 2
 
 
 @pytest.mark.parametrize("E,M", WIDE)
-@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+@pytest.mark.parametrize("rnd", MODES)
 def test_circuit_wide_sampled(E, M, rnd):
     n = 1 << 15
     B = 1 + E + M
@@ -134,7 +137,7 @@ def test_generated_formats_match_the_build_list():
 
 
 @pytest.mark.parametrize("op", ["add", "sub", "mul"])
-@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+@pytest.mark.parametrize("rnd", MODES)
 def test_generated_netlist_exhaustive_1_4_3(op, rnd):
     a, b = synth.all_pairs(8)
     a, b = a.astype(np.uint32), b.astype(np.uint32)
@@ -144,7 +147,7 @@ def test_generated_netlist_exhaustive_1_4_3(op, rnd):
 
 
 @pytest.mark.parametrize("E,M", GEN)
-@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+@pytest.mark.parametrize("rnd", MODES)
 def test_generated_netlist_sampled(E, M, rnd):
     n = 1 << 14
     B = 1 + E + M

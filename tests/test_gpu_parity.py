@@ -181,6 +181,51 @@ def test_every_launch_variant(E, M):
         bs.bsfp_set_variant(f, op, 0, 0)
 
 
+# ----------------------------------------------------- flush to zero ---
+FTZ_MODES = [oracle.RN_FTZ, oracle.RZ_FTZ]
+
+
+@pytest.mark.parametrize("rnd", FTZ_MODES)
+def test_flush_to_zero_exhaustive_1_4_3(rnd):
+    a, b = synth.all_pairs(8)
+    for op in ("add", "sub", "mul"):
+        check(op, 4, 3, rnd, a, b)
+    i = np.arange(1 << 24, dtype=np.uint32)
+    check("fma2", 4, 3, rnd, i >> 16, (i >> 8) & 255, i & 255)
+
+
+@pytest.mark.parametrize("E,M", TUNED)
+@pytest.mark.parametrize("rnd", FTZ_MODES)
+def test_flush_to_zero_tuned_formats(E, M, rnd):
+    """Seeded values of the workload recipe, uniform encodings, and operands
+    whose exponent fields sit at the bottom of the range (subnormal operands,
+    tiny products and sums), in every compiled launch variant."""
+    n = 60_000 + 7
+    B = 1 + E + M
+    r = synth.splitmix64(7700 + E * 32 + M, 3 * n)
+    low = ((r % np.uint64(1 << (M + 1))) | ((r >> np.uint64(40)) % np.uint64(3) << np.uint64(M + 1))
+           | ((r >> np.uint64(50)) & np.uint64(1)) << np.uint64(B - 1)).astype(np.uint32)
+    a = np.concatenate([synth.fp_values(E, M, n, 71).astype(np.uint32), synth.uniform_bits(B, n, 72).astype(np.uint32),
+                        low[:n]])
+    b = np.concatenate([synth.fp_values(E, M, n, 73).astype(np.uint32), synth.uniform_bits(B, n, 74).astype(np.uint32),
+                        low[n:2 * n]])
+    c = np.concatenate([synth.fp_values(E, M, n, 75).astype(np.uint32), synth.uniform_bits(B, n, 76).astype(np.uint32),
+                        low[2 * n:]])
+    f = bs.Format(E, M, rnd)
+    for op in OPS:
+        for wpt in bs.bsfp_variants_compiled(f, op):
+            check(op, E, M, rnd, a, b, c if op == "fma2" else None, wpt=wpt)
+        bs.bsfp_set_variant(f, op, 0, 0)
+
+
+def test_flush_to_zero_is_refused_where_not_compiled():
+    f = bs.Format(6, 9, oracle.RN_FTZ)
+    x = torch.zeros(16 * 32, dtype=torch.int32, device="cuda")
+    with pytest.raises(bs.BsfpError) as ei:
+        bs.bsfp_add(f, x, x, x, 10)
+    assert ei.value.status == bs.ERR_UNSUPPORTED
+
+
 # ------------------------------------------------------------ edge cases ---
 @pytest.mark.parametrize("n", [1, 31, 32, 33, 1023, 1025, 32 * 1024 - 1, 32 * 1024 + 1])
 def test_tail_lengths(n):

@@ -4,12 +4,14 @@ The oracle (``oracle/bsfp_oracle.c``) is checked against things that do not
 depend on it:
 
 * the brute-force Fraction checker (``oracle/bruteforce.py``), exhaustively
-  over every operand pair of small formats (add, sub, mul; RN and RZ);
+  over every operand pair of small formats (add, sub, mul; RN and RZ, and both
+  with flush to zero, where it searches the normal values only);
 * hand-derived values in ``tests/golden/`` (Sec. 5.2's 1/4/3 format, Sec. 2's
   Fig. 1 layout);
 * the host FPU: IEEE binary16 through numpy (1/5/10, the paper's FP16),
   binary32 through C ``fesetround`` (1/8/23, the paper's FP32), bfloat16 through
-  torch (1/8/7);
+  torch (1/8/7), and binary32 with the CPU's flush-to-zero and
+  denormals-are-zero modes through torch (1/8/23 with flush to zero);
 * a neighbour check of correct rounding for every sweep format
   (E 3..8 x M 2..23): the result's encoding neighbours bracket the exact value
   as RN-even / RZ require;
@@ -39,7 +41,7 @@ SMALL_FORMATS = [(2, 1), (2, 3), (3, 2), (3, 3), (2, 5), (3, 4), (4, 3), (5, 2)]
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("E,M", SMALL_FORMATS)
 @pytest.mark.parametrize("op", ["add", "sub", "mul"])
-@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ])
 def test_exhaustive_vs_bruteforce(E, M, op, rnd):
     F = bf.fmt(E, M)
     a, b = synth.all_pairs(F.B)
@@ -53,7 +55,7 @@ def test_exhaustive_vs_bruteforce(E, M, op, rnd):
 
 
 @pytest.mark.parametrize("E,M", [(4, 3), (3, 3), (4, 4)])
-@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ])
 def test_fma2_vs_bruteforce_sampled(E, M, rnd):
     F = bf.fmt(E, M)
     n = 6000
@@ -228,6 +230,53 @@ def test_binary32_vs_host_fenv(op, rnd):
     ok = H.nan_class_equal(8, 23, got, want)
     assert ok.all(), "first mismatch %#x %#x got %#x want %#x" % (
         a[~ok][0], b[~ok][0], got[~ok][0], want[~ok][0])
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+def test_binary32_flush_to_zero_vs_host(op):
+    """1/8/23 RN with flush to zero against the host FPU's binary32 with
+    flush-to-zero and denormals-are-zero set (torch.set_flush_denormal).  A
+    product whose exact magnitude lies in [2^-126 (1 - 2^-24), 2^-126) is
+    tiny before rounding but rounds to the smallest normal, so FPUs that judge
+    tininess after rounding keep it: those few pairs are left out (sums of
+    flushed operands are exact, so add and sub have no such band)."""
+    torch = pytest.importorskip("torch")
+    n = 1 << 16
+    # exponent fields near the bottom of the range, so that subnormal operands
+    # and tiny results are common, plus uniform bit patterns
+    r = synth.splitmix64(61, 8 * n)
+    low = lambda k: ((r[k::8] & np.uint64(0x807FFFFF)) |
+                     ((r[k + 4::8] % np.uint64(70)) << np.uint64(23))).astype(np.uint32)
+    a = np.concatenate([low(0), synth.splitmix64(62, n, 0).astype(np.uint32)])
+    b = np.concatenate([low(1), synth.splitmix64(62, n, 1).astype(np.uint32)])
+    if op == "add":   # cancellation towards the bottom of the range
+        b[:n // 4] = (a[:n // 4] ^ 0x80000000) ^ (low(3)[:n // 4] & 0x3F)
+    old_threads = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        if not torch.set_flush_denormal(True):
+            pytest.skip("the host cannot flush denormals")
+        ta = torch.from_numpy(a.view(np.float32).copy())
+        tb = torch.from_numpy(b.view(np.float32).copy())
+        tr = {"add": ta + tb, "sub": ta - tb, "mul": ta * tb}[op]
+        want = tr.numpy().view(np.uint32).astype(np.uint32)
+    finally:
+        torch.set_flush_denormal(False)
+        torch.set_num_threads(old_threads)
+    got = oracle.binop(op, 8, 23, oracle.RN_FTZ, a, b)
+    keep = np.ones(a.size, bool)
+    if op == "mul":
+        fa = np.where((a >> 23) & 0xFF, a.view(np.float32), 0).astype(np.float64)
+        fb = np.where((b >> 23) & 0xFF, b.view(np.float32), 0).astype(np.float64)
+        ex = np.abs(fa * fb)                                 # exact: 48-bit products fit in a double
+        keep = ~((ex < 2.0 ** -126) & (ex >= 2.0 ** -126 * (1 - 2.0 ** -24)))
+    ok = H.nan_class_equal(8, 23, got, want) | ~keep
+    assert keep.sum() > a.size - 16
+    assert ok.all(), "first mismatch %#x %#x got %#x want %#x" % (
+        a[~ok][0], b[~ok][0], got[~ok][0], want[~ok][0])
+    # flushing changed something: the sample does reach the subnormal range
+    plain = oracle.binop(op, 8, 23, oracle.RN, a, b)
+    assert (plain != got).sum() > 100
 
 
 def test_bfloat16_rn_vs_torch():
