@@ -33,7 +33,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OPS = {"add": 0, "sub": 1, "mul": 2, "fma2": 3}
+OPS = {"add": 0, "sub": 1, "mul": 2, "fma2": 3, "div": 4}
 RN, RZ, RN_FTZ, RZ_FTZ = 0, 1, 2, 3   # rounding modes; bit 1 = flush to zero
 
 
@@ -55,7 +55,7 @@ def lib():
             L = ctypes.CDLL(path)
             u32, i32, i64 = ctypes.c_uint32, ctypes.c_int, ctypes.c_int64
             p = ctypes.c_void_p
-            for name in ("oracle_add1", "oracle_sub1", "oracle_mul1"):
+            for name in ("oracle_add1", "oracle_sub1", "oracle_mul1", "oracle_div1"):
                 fn = getattr(L, name)
                 fn.argtypes = [i32, i32, i32, u32, u32]
                 fn.restype = u32
@@ -84,7 +84,7 @@ def _ptr(a: np.ndarray):
 
 
 def binop(op: str, E: int, M: int, rnd: int, a, b, c=None) -> np.ndarray:
-    """Element-wise ``op`` in {add, sub, mul, fma2} on B-bit patterns (uint32)."""
+    """Element-wise ``op`` in {add, sub, mul, fma2, div} on B-bit patterns (uint32)."""
     a, b = _u32(a), _u32(b)
     assert a.shape == b.shape
     c = _u32(c) if c is not None else np.zeros_like(a)
@@ -103,6 +103,10 @@ def sub(E, M, rnd, a, b):
 
 def mul(E, M, rnd, a, b):
     return binop("mul", E, M, rnd, a, b)
+
+
+def div(E, M, rnd, a, b):
+    return binop("div", E, M, rnd, a, b)
 
 
 def fma2(E, M, rnd, a, b, c):

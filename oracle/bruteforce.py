@@ -152,6 +152,26 @@ class Format:
         # a nonzero product that rounds to zero keeps the sign of the exact result
         return r
 
+    def div(self, x: int, y: int, rnd: int) -> int:
+        """IEEE-754 division: NaN for NaN operands, 0/0 and Inf/Inf; x/0 and
+        Inf/y are infinities, x/Inf and 0/y zeros, signed by XOR."""
+        if self.is_nan(x) or self.is_nan(y):
+            return self.nan
+        s = self.fields(x)[0] ^ self.fields(y)[0]
+        xi, yi = self.is_inf(x), self.is_inf(y)
+        if xi and yi:
+            return self.nan
+        if xi:
+            return self.inf(s)
+        if yi:
+            return s * self.sign_bit
+        vx, vy = self.operand(x, rnd), self.operand(y, rnd)
+        if vy == 0:
+            return self.nan if vx == 0 else self.inf(s)
+        if vx == 0:
+            return s * self.sign_bit
+        return self.round(vx / vy, rnd)
+
     def fma2(self, x: int, y: int, z: int, rnd: int) -> int:
         return self.add(self.mul(x, y, rnd), z, rnd)
 

@@ -271,6 +271,31 @@ static uint32_t o_mul(const fmt_t *f, uint32_t x, uint32_t y) {
     return round_encode(f, s, &T, a.q + b.q);
 }
 
+/* x / y, one rounding (the division of Sec. 4, Table 1).  IEEE-754 cases:
+ * NaN for a NaN operand, 0/0 and Inf/Inf; x/0 = Inf and x/Inf = 0 with the
+ * sign of x*y.  Otherwise the exact quotient mant_x / mant_y * 2^(qx - qy)
+ * becomes T * 2^q with K = 2M + 8 extra quotient bits, whose lowest bit is
+ * set when the division leaves a remainder: T has at least M + 9 bits, so
+ * that bit lies at least seven places below the rounding position and only
+ * records "inexact", which is all that rounding needs from the bits below. */
+static uint32_t o_div(const fmt_t *f, uint32_t x, uint32_t y) {
+    val_t a = decode(f, x), b = decode(f, y);
+    int s = a.s ^ b.s;
+    if (a.cls == CLS_NAN || b.cls == CLS_NAN) return canonical_nan(f);
+    if (a.cls == CLS_INF) return b.cls == CLS_INF ? canonical_nan(f) : infinity(f, s);
+    if (b.cls == CLS_INF) return enc(f, s, 0, 0);
+    if (b.mant == 0) return a.mant == 0 ? canonical_nan(f) : infinity(f, s);
+    if (a.mant == 0) return enc(f, s, 0, 0);
+    const int K = 2 * f->M + 8;                      /* <= 54: the numerator fits in 128 bits */
+    unsigned __int128 num = (unsigned __int128)a.mant << K;
+    unsigned __int128 quo = num / b.mant, rem = num % b.mant;
+    quo = (quo << 1) | (rem != 0);
+    big T; big_zero(&T);
+    T.w[0] = (uint64_t)quo;
+    T.w[1] = (uint64_t)(quo >> 64);
+    return round_encode(f, s, &T, a.q - b.q - K - 1);
+}
+
 static uint32_t flip_sign(const fmt_t *f, uint32_t y) { return y ^ (1u << (f->E + f->M)); }
 
 /* ------------------------------------------------------------------------ */
@@ -280,12 +305,13 @@ static uint32_t flip_sign(const fmt_t *f, uint32_t y) { return y ^ (1u << (f->E 
 uint32_t oracle_add1(int E, int M, int rz, uint32_t x, uint32_t y) { fmt_t f = mkfmt(E, M, rz); return o_add(&f, x, y); }
 uint32_t oracle_sub1(int E, int M, int rz, uint32_t x, uint32_t y) { fmt_t f = mkfmt(E, M, rz); return o_add(&f, x, flip_sign(&f, y)); }
 uint32_t oracle_mul1(int E, int M, int rz, uint32_t x, uint32_t y) { fmt_t f = mkfmt(E, M, rz); return o_mul(&f, x, y); }
+uint32_t oracle_div1(int E, int M, int rz, uint32_t x, uint32_t y) { fmt_t f = mkfmt(E, M, rz); return o_div(&f, x, y); }
 uint32_t oracle_fma2_1(int E, int M, int rz, uint32_t x, uint32_t y, uint32_t z) {
     fmt_t f = mkfmt(E, M, rz);
     return o_add(&f, o_mul(&f, x, y), z);
 }
 
-/* op: 0 add, 1 sub, 2 mul, 3 fma2 (a*b rounded, then + c rounded) */
+/* op: 0 add, 1 sub, 2 mul, 3 fma2 (a*b rounded, then + c rounded), 4 div */
 void oracle_binop(int op, int E, int M, int rz, const uint32_t *a, const uint32_t *b,
                   const uint32_t *c, uint32_t *out, int64_t n) {
     fmt_t f = mkfmt(E, M, rz);
@@ -296,6 +322,7 @@ void oracle_binop(int op, int E, int M, int rz, const uint32_t *a, const uint32_
         case 0: r = o_add(&f, a[i], b[i]); break;
         case 1: r = o_add(&f, a[i], flip_sign(&f, b[i])); break;
         case 2: r = o_mul(&f, a[i], b[i]); break;
+        case 4: r = o_div(&f, a[i], b[i]); break;
         default: r = o_add(&f, o_mul(&f, a[i], b[i]), c[i]); break;
         }
         out[i] = r;

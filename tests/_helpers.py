@@ -22,7 +22,7 @@ _fenv = None
 
 
 def host_f32(op: str, rz: int, a, b) -> np.ndarray:
-    """Host FPU binary32 add/mul in RN or RZ (pin for 1/8/23)."""
+    """Host FPU binary32 add/mul/div in RN or RZ (pin for 1/8/23)."""
     global _fenv
     if _fenv is None:
         path = build_c(os.path.join(HERE, "host_fenv.c"), "fenv",
@@ -34,7 +34,7 @@ def host_f32(op: str, rz: int, a, b) -> np.ndarray:
     a = np.ascontiguousarray(a, dtype=np.uint32)
     b = np.ascontiguousarray(b, dtype=np.uint32)
     out = np.empty_like(a)
-    _fenv.host_f32({"add": 0, "mul": 1}[op], rz, a.ctypes.data, b.ctypes.data, out.ctypes.data, a.size)
+    _fenv.host_f32({"add": 0, "mul": 1, "div": 2}[op], rz, a.ctypes.data, b.ctypes.data, out.ctypes.data, a.size)
     return out
 
 

@@ -40,7 +40,7 @@ SMALL_FORMATS = [(2, 1), (2, 3), (3, 2), (3, 3), (2, 5), (3, 4), (4, 3), (5, 2)]
 # brute force, exhaustive
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("E,M", SMALL_FORMATS)
-@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 @pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ])
 def test_exhaustive_vs_bruteforce(E, M, op, rnd):
     F = bf.fmt(E, M)
@@ -180,28 +180,35 @@ def _f16_operands():
     return np.concatenate([a1, a2, a3, sa]), np.concatenate([b1, b2, b3, sb])
 
 
-@pytest.mark.parametrize("op", ["add", "mul"])
+@pytest.mark.parametrize("op", ["add", "mul", "div"])
 def test_binary16_rn_vs_numpy(op):
+    """numpy computes a binary16 result in binary32 and rounds it to binary16;
+    that double rounding is innocuous for +, * and / since 24 >= 2 * 11 + 2
+    (Figueroa's theorem)."""
     a, b = _f16_operands()
     fa = a.astype(np.uint16).view(np.float16)
     fb = b.astype(np.uint16).view(np.float16)
     with np.errstate(all="ignore"):
-        ref = (fa + fb) if op == "add" else (fa * fb)
+        ref = {"add": fa + fb, "mul": fa * fb, "div": fa / fb}[op]
     want = ref.view(np.uint16).astype(np.uint32)
     got = oracle.binop(op, 5, 10, oracle.RN, a, b)
     ok = H.nan_class_equal(5, 10, got, want)
     assert ok.all(), "first mismatch %#x %#x" % (a[~ok][0], b[~ok][0])
 
 
-@pytest.mark.parametrize("op", ["add", "mul"])
+@pytest.mark.parametrize("op", ["add", "mul", "div"])
 def test_binary16_rz_vs_exact_double(op):
     """binary16 sums and products are exact in binary64; truncating that exact
-    value toward zero is the RZ result."""
+    value toward zero is the RZ result.  Quotients are not exact, but a
+    quotient of two binary16 values that is not itself a binary16 value lies
+    at least 2^-22 (relative) from every binary16 value, far more than the
+    2^-53 of the binary64 rounding, so truncating the binary64 quotient gives
+    the same binary16 value."""
     a, b = _f16_operands()
     fa = a.astype(np.uint16).view(np.float16).astype(np.float64)
     fb = b.astype(np.uint16).view(np.float16).astype(np.float64)
     with np.errstate(all="ignore"):
-        ex = (fa + fb) if op == "add" else (fa * fb)
+        ex = {"add": fa + fb, "mul": fa * fb, "div": fa / fb}[op]
         r = ex.astype(np.float16)                          # correctly rounded (RN)
         over = np.abs(r.astype(np.float64)) > np.abs(ex)   # RN went away from zero
         r = np.where(over, np.nextafter(r, np.float16(0)), r)
@@ -213,7 +220,7 @@ def test_binary16_rz_vs_exact_double(op):
         a[~ok][0], b[~ok][0], got[~ok][0], want[~ok][0])
 
 
-@pytest.mark.parametrize("op", ["add", "mul"])
+@pytest.mark.parametrize("op", ["add", "mul", "div"])
 @pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
 def test_binary32_vs_host_fenv(op, rnd):
     n = 1 << 17
@@ -289,8 +296,8 @@ def test_bfloat16_rn_vs_torch():
     b = np.concatenate([synth.uniform_bits(16, n, 41, 1), synth.fp_values(8, 7, n, 42, 1)]).astype(np.uint32)
     ta = torch.from_numpy(a.astype(np.int32).astype(np.int16)).view(torch.bfloat16)
     tb = torch.from_numpy(b.astype(np.int32).astype(np.int16)).view(torch.bfloat16)
-    for op in ("add", "mul"):
-        r = (ta + tb) if op == "add" else (ta * tb)
+    for op in ("add", "mul", "div"):
+        r = {"add": ta + tb, "mul": ta * tb, "div": ta / tb}[op]   # binary32 result rounded: 24 >= 2*8+2
         want = r.view(torch.int16).numpy().astype(np.uint16).astype(np.uint32)
         got = oracle.binop(op, 8, 7, oracle.RN, a, b)
         ok = H.nan_class_equal(8, 7, got, want)
