@@ -80,7 +80,7 @@ typedef enum {
 } bsfp_status;
 
 /* Operation codes (bsfp_op_name, batch jobs, autotune, gate count). */
-typedef enum { BSFP_OP_ADD = 0, BSFP_OP_SUB = 1, BSFP_OP_MUL = 2, BSFP_OP_FMA2 = 3 } bsfp_op;
+typedef enum { BSFP_OP_ADD = 0, BSFP_OP_SUB = 1, BSFP_OP_MUL = 2, BSFP_OP_FMA2 = 3, BSFP_OP_DIV = 4 } bsfp_op;
 
 #define BSFP_MAX_N (((int64_t)1) << 40)
 
@@ -118,6 +118,12 @@ bsfp_status bsfp_mul(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32
  * register reuse follows the locality advice of Sec. 4. */
 bsfp_status bsfp_fma2(bsfp_format f, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out,
                       int64_t n, bsfp_stream_t s);
+/* out = a / b, one rounding (Sec. 4, Table 1 row Div: restoring division).
+ * IEEE-754 cases: NaN for a NaN operand, 0/0 and Inf/Inf; x/0 and Inf/y are
+ * infinities and 0/y, x/Inf zeros, each with the XOR of the signs.  Runs as a
+ * plain kernel inside batch plans, the no-allocation launch and the server. */
+bsfp_status bsfp_div(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                     bsfp_stream_t s);
 
 /* -------------------------------------------------------------- batched --- */
 /* One element-wise op on one vector: the unit of a batch.  c is used by

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbsfp.so")
 
 RN, RZ, RN_FTZ, RZ_FTZ = 0, 1, 2, 3
-OP_ADD, OP_SUB, OP_MUL, OP_FMA2 = 0, 1, 2, 3
-OPS = {"add": OP_ADD, "sub": OP_SUB, "mul": OP_MUL, "fma2": OP_FMA2}
+OP_ADD, OP_SUB, OP_MUL, OP_FMA2, OP_DIV = 0, 1, 2, 3, 4
+OPS = {"add": OP_ADD, "sub": OP_SUB, "mul": OP_MUL, "fma2": OP_FMA2, "div": OP_DIV}
 
 OK = 0
 ERR_FORMAT, ERR_NULL, ERR_ALIGN, ERR_SIZE, ERR_UNSUPPORTED, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT = range(-1, -9, -1)
@@ -110,6 +110,7 @@ def _lib():
                 "bsfp_sub": (i32, [F, p, p, p, i64, p]),
                 "bsfp_mul": (i32, [F, p, p, p, i64, p]),
                 "bsfp_fma2": (i32, [F, p, p, p, p, i64, p]),
+                "bsfp_div": (i32, [F, p, p, p, i64, p]),
                 "bsfp_status_str": (ctypes.c_char_p, [i32]),
                 "bsfp_last_cuda_error": (i32, []),
                 "bsfp_gate_count": (i64, [F, i32]),
@@ -220,11 +221,15 @@ def bsfp_fma2(f, a, b, c, out, n: int, stream=None):
     _check(_lib().bsfp_fma2(_fmt(f), _ptr(a), _ptr(b), _ptr(c), _ptr(out), n, _stream(stream)), "bsfp_fma2")
 
 
+def bsfp_div(f, a, b, out, n: int, stream=None):
+    _check(_lib().bsfp_div(_fmt(f), _ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "bsfp_div")
+
+
 def bsfp_op(op: str, f, a, b, out, n: int, c=None, stream=None):
-    """Dispatch by name: add, sub, mul or fma2."""
+    """Dispatch by name: add, sub, mul, fma2 or div."""
     if op == "fma2":
         return bsfp_fma2(f, a, b, c, out, n, stream)
-    return {"add": bsfp_add, "sub": bsfp_sub, "mul": bsfp_mul}[op](f, a, b, out, n, stream)
+    return {"add": bsfp_add, "sub": bsfp_sub, "mul": bsfp_mul, "div": bsfp_div}[op](f, a, b, out, n, stream)
 
 
 # ---------------------------------------------------------- diagnostics ---

@@ -22,7 +22,7 @@
 
 namespace bsfp {
 
-BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_COUNT];
+BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_ALL];
 
 /* Each exponent width is compiled as two translation units, M in [1, 11]
  * and [12, 23]; each fills its part of the table. */
@@ -51,8 +51,8 @@ struct Shape {
     int8_t wpt;
     int16_t bps;
 };
-static Shape g_shape[TAB_E][TAB_M][TAB_R][OPC_COUNT];
-static int g_occ[TAB_E][TAB_M][TAB_R][OPC_COUNT][5];   /* cached occupancy per wpt */
+static Shape g_shape[TAB_E][TAB_M][TAB_R][OPC_ALL];
+static int g_occ[TAB_E][TAB_M][TAB_R][OPC_ALL][5];   /* cached occupancy per wpt */
 static std::mutex g_shape_mu;
 
 static std::atomic<int64_t> g_launches{0};
@@ -78,6 +78,7 @@ int opclass(int op) {
         case BSFP_OP_SUB: return OPC_ADDSUB;
         case BSFP_OP_MUL: return OPC_MUL;
         case BSFP_OP_FMA2: return OPC_FMA2;
+        case BSFP_OP_DIV: return OPC_DIV;
     }
     return -1;
 }
@@ -234,6 +235,10 @@ bsfp_status bsfp_fma2(bsfp_format f, const uint32_t* a, const uint32_t* b, const
     return run_binop(f, BSFP_OP_FMA2, a, b, c, out, n, (cudaStream_t)s);
 }
 
+bsfp_status bsfp_div(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n, bsfp_stream_t s) {
+    return run_binop(f, BSFP_OP_DIV, a, b, nullptr, out, n, (cudaStream_t)s);
+}
+
 const char* bsfp_status_str(int32_t status) {
     switch (status) {
         case BSFP_OK: return "ok";
@@ -260,7 +265,7 @@ long bsfp_gate_count_e7(int, int, int);
 long bsfp_gate_count_e8(int, int, int);
 
 int64_t bsfp_gate_count(bsfp_format f, int32_t op) {
-    if (!format_ok(f) || op < 0 || op > 3) return -1;
+    if (!format_ok(f) || op < 0 || op > 4) return -1;
     const int m = f.man_bits, r = f.rnd;
     switch (f.exp_bits) {
         case 2: return bsfp_gate_count_e2(m, r, op);

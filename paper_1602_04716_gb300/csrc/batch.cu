@@ -82,7 +82,7 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         const bsfp_job& j = jobs[i];
         const bsfp_status st = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &prep[(size_t)i]);
         if (st != BSFP_OK) return st;
-        if (o.mode == BSFP_BATCH_PERSISTENT && !prep[(size_t)i].skip &&
+        if (o.mode == BSFP_BATCH_PERSISTENT && !prep[(size_t)i].skip && prep[(size_t)i].opc < OPC_COUNT &&
             batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0)
             group[(size_t)i] = prep[(size_t)i].opc;
     }

@@ -239,7 +239,7 @@ extern "C" bsfp_status bsfp_batch_run_noalloc(const bsfp_job* jobs, int32_t njob
         const bsfp_status v = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &po);
         if (v != BSFP_OK) return v;
         if (po.skip) continue;
-        if (batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) < 0) {
+        if (po.opc >= OPC_COUNT || batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) < 0) {
             any_plain = true;
             continue;
         }
@@ -294,7 +294,7 @@ extern "C" bsfp_status bsfp_batch_run_noalloc(const bsfp_job* jobs, int32_t njob
     /* jobs outside the persistent formats: their plain kernels */
     for (int32_t i = 0; i < njobs && any_plain && rc == BSFP_OK; ++i) {
         const bsfp_job& j = jobs[i];
-        if (batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0) continue;
+        if (opclass(j.op) < OPC_COUNT && batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0) continue;
         PreparedOp po;
         rc = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &po);
         if (rc == BSFP_OK && !po.skip) {

@@ -28,8 +28,10 @@
 
 namespace bsfp {
 
-/* Operation classes with a kernel of their own (sub shares the adder). */
-enum OpClass : int { OPC_ADDSUB = 0, OPC_MUL = 1, OPC_FMA2 = 2, OPC_COUNT = 3 };
+/* Operation classes with a kernel of their own (sub shares the adder).  The
+ * batched persistent kernels cover the first OPC_COUNT classes; division
+ * runs as its plain kernel everywhere. */
+enum OpClass : int { OPC_ADDSUB = 0, OPC_MUL = 1, OPC_FMA2 = 2, OPC_COUNT = 3, OPC_DIV = 3, OPC_ALL = 4 };
 
 struct BinopArgs {
     const uint32_t* a;
@@ -86,6 +88,8 @@ __device__ __forceinline__ void column_op(uint32_t* x, uint32_t* y, const uint32
         fp_add<E, M, RZ, false, FTZ>(x, y, r);
     } else if constexpr (OPC == OPC_MUL) {
         fp_mul<E, M, RZ, FTZ>(x, y, r);
+    } else if constexpr (OPC == OPC_DIV) {
+        fp_div<E, M, RZ, FTZ>(x, y, r);
     } else {
         uint32_t p[B];
         fp_mul<E, M, RZ, FTZ>(x, y, p);
@@ -204,6 +208,6 @@ constexpr BinopEntry make_entry() {
 /* Table of every compiled (E, M, rounding, op class); filled by the
  * per-exponent translation units. */
 constexpr int TAB_E = 9, TAB_M = 24, TAB_R = 4;
-extern BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_COUNT];
+extern BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_ALL];
 
 }  // namespace bsfp

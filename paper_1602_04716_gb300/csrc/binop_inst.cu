@@ -3,8 +3,8 @@
  * width.  The build compiles this file once per E in [2, 8] with -DBSFP_E=E,
  * so the 7 translation units build in parallel; each fills its slice of the
  * dispatch table for M in [BSFP_M_LO, BSFP_M_HI], both rounding modes (and
- * their flush-to-zero forms for the tuned formats) and the three kernel
- * classes (add/sub, mul, fma2).  This replaces the paper's
+ * their flush-to-zero forms for the tuned formats) and the four kernel
+ * classes (add/sub, mul, fma2, div).  This replaces the paper's
  * library generator (Sec. 5.1), which emitted code per configured format.
  */
 #include "binop.cuh"
@@ -26,6 +26,7 @@ static void fill_mode() {
     g_binop_table[E][M][R][OPC_ADDSUB] = make_entry<E, M, R, OPC_ADDSUB>();
     g_binop_table[E][M][R][OPC_MUL] = make_entry<E, M, R, OPC_MUL>();
     g_binop_table[E][M][R][OPC_FMA2] = make_entry<E, M, R, OPC_FMA2>();
+    g_binop_table[E][M][R][OPC_DIV] = make_entry<E, M, R, OPC_DIV>();
 }
 
 template <int E, int M>

@@ -614,8 +614,183 @@ template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void fp_mul(
     encode<E, M, NU, RZ>(mag, OR(aspec, bspec), nan, zero, s, W(0u), r);
 }
 
+/* ------------------------------------------------------------------ div --- */
+BSFP_HDC constexpr int bit_length(int v) { return v <= 0 ? 0 : 1 + bit_length(v >> 1); }
+
+/* r = a / b, one rounding (Sec. 4, Table 1, Div: restoring division).
+ * 1. Both significands (implicit bit included) are normalised left by the
+ *    log shifter, so that a subnormal operand has its leading one on top;
+ *    the exponents become max(e,1) - shift.
+ * 2. Restoring division: M+3 quotient bits of X / Y, most significant first,
+ *    each a borrow chain R - Y (the bit is 1 when nothing is borrowed) and a
+ *    multiplexer keeping R or R - Y, then a doubling of R; the final R != 0
+ *    is the sticky bit.
+ * 3. X / Y lies in (1/2, 2): the first quotient bit selects a one-position
+ *    normalisation; the exponent field before rounding is
+ *    ex' - ey' + bias - 1 + (first bit).
+ * 4. Below the normal range the significand, guard and sticky shift right
+ *    into the subnormal positions (a fixed shift by one, then the log
+ *    shifter by the complement of the exponent), as in the multiplier.
+ * 5. Rounding, overflow and the IEEE cases: NaN for NaN operands, 0/0 and
+ *    Inf/Inf; x/0 and Inf/y are infinities, 0/y and x/Inf zeros, the sign
+ *    the XOR of the signs.
+ * With flush to zero the operands are normal or zero, step 1 and step 4
+ * disappear, and a result below the normal range is a zero of its sign. */
+template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void fp_div(const W* a, const W* b, W* r) {
+    static_assert(E >= 2 && M >= 1 && 1 + E + M <= 32, "format out of range");
+    constexpr int B = 1 + E + M;
+    constexpr int N1 = M + 1;
+    constexpr int KT = floor_log2(N1 - 1);                           /* shift counts have KT+1 bits */
+    constexpr int NU = bit_length((1 << (E + 1)) + 2 * M + 16) + 1;  /* signed exponent width */
+    constexpr int NQ = M + 3;                                        /* quotient bits */
+    const W s = XOR(a[B - 1], b[B - 1]);
+    const W* ea = a + M;
+    const W* eb = b + M;
+    const W nzA = or_n<E>(ea), nzB = or_n<E>(eb);
+    const W fA = or_n<M>(a), fB = or_n<M>(b);
+    const W aspec = and_n<E>(ea), bspec = and_n<E>(eb);
+
+    /* step 1: significands, normalised */
+    W X[N1], Y[N1];
+    BSFP_UNROLL
+    for (int i = 0; i < M; ++i) {
+        X[i] = a[i];
+        Y[i] = b[i];
+    }
+    W tx[KT + 1], ty[KT + 1];
+    if constexpr (FTZ) {
+        X[M] = ~W(0u);
+        Y[M] = ~W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i <= KT; ++i) tx[i] = ty[i] = W(0u);
+    } else {
+        X[M] = nzA;
+        Y[M] = nzB;
+        W ones[KT + 1];
+        BSFP_UNROLL
+        for (int i = 0; i <= KT; ++i) ones[i] = ~W(0u);
+        lnorm<N1, KT + 1>(X, ones, tx);
+        lnorm<N1, KT + 1>(Y, ones, ty);
+    }
+
+    /* exponents: P1 = max(ea,1) + ty, P2 = max(eb,1) + tx (NU bits), then
+     * D = P1 - P2 + bias - 2 + top = P1 + ~P2 + (bias - 1) + top: a carry-save
+     * step of P1, ~P2 and the constant, a ripple adder with top as carry-in */
+    W P1[NU], P2[NU];
+    {
+        W c1 = W(0u), c2 = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            const W xa = (i == 0) ? OR(ea[0], NOT(nzA)) : (i < E ? ea[(i < E) ? i : 0] : W(0u));
+            const W xb = (i == 0) ? OR(eb[0], NOT(nzB)) : (i < E ? eb[(i < E) ? i : 0] : W(0u));
+            const W sy = (i <= KT) ? ty[(i <= KT) ? i : 0] : W(0u);
+            const W sx = (i <= KT) ? tx[(i <= KT) ? i : 0] : W(0u);
+            P1[i] = XOR3(xa, sy, c1);
+            P2[i] = XOR3(xb, sx, c2);
+            c1 = MAJ(xa, sy, c1);
+            c2 = MAJ(xb, sx, c2);
+        }
+    }
+
+    /* step 2: restoring division, Q[NQ-1] first (weight 2^(M+2)) */
+    W R[M + 2], Q[NQ];
+    BSFP_UNROLL
+    for (int i = 0; i < N1; ++i) R[i] = X[i];
+    R[M + 1] = W(0u);
+    BSFP_UNROLL
+    for (int j = 0; j < NQ; ++j) {
+        W d[M + 2];
+        W br = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < M + 2; ++i) {
+            const W yi = (i < N1) ? Y[(i < N1) ? i : 0] : W(0u);
+            d[i] = XOR3(R[i], yi, br);
+            br = MAJ(NOT(R[i]), yi, br);
+        }
+        const W q = NOT(br);
+        Q[NQ - 1 - j] = q;
+        BSFP_UNROLL
+        for (int i = 0; i < M + 2; ++i) R[i] = MUX(q, d[i], R[i]);
+        if (j + 1 < NQ) {
+            BSFP_UNROLL
+            for (int i = M + 1; i > 0; --i) R[i] = R[i - 1];
+            R[0] = W(0u);
+        }
+    }
+    const W rem = or_n<M + 2>(R);
+
+    /* step 3: normalisation and the exponent */
+    const W top = Q[NQ - 1];
+    W sig[N1];
+    BSFP_UNROLL
+    for (int i = 0; i < N1; ++i) sig[i] = MUX(top, Q[i + 2], Q[i + 1]);
+    const W g = MUX(top, Q[1], Q[0]);
+    const W st = ANDOR(top, Q[0], rem);
+    constexpr uint32_t KB = (uint32_t)((1 << (E - 1)) - 2) & ((1u << NU) - 1u);   /* bias - 1 */
+    W D[NU];
+    {
+        W cs[NU], cc[NU + 1];
+        cc[0] = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            const W x1 = P1[i], x2 = NOT(P2[i]);
+            const bool k = (KB >> i) & 1u;
+            cs[i] = k ? NOT(XOR(x1, x2)) : XOR(x1, x2);
+            cc[i + 1] = k ? OR(x1, x2) : AND(x1, x2);
+        }
+        W c = top;
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            D[i] = XOR3(cs[i], cc[i], c);
+            if (i + 1 < NU) c = MAJ(cs[i], cc[i], c);
+        }
+    }
+    const W neg = D[NU - 1];   /* exponent field before rounding < 1 */
+
+    /* step 4: below the normal range (gradual underflow) */
+    W sigf[N1], Df[NU - 1];
+    W gf = g, stf = st;
+    if constexpr (FTZ) {
+        BSFP_UNROLL
+        for (int i = 0; i < N1; ++i) sigf[i] = sig[i];
+        BSFP_UNROLL
+        for (int i = 0; i < NU - 1; ++i) Df[i] = D[i];
+    } else {
+        constexpr int NS = M + 3;
+        W q[NS];
+        q[0] = OR(st, g);
+        BSFP_UNROLL
+        for (int p = 1; p <= M + 1; ++p) q[p] = sig[p - 1];
+        q[NS - 1] = W(0u);
+        W nd[NU - 1];
+        BSFP_UNROLL
+        for (int i = 0; i < NU - 1; ++i) nd[i] = NOT(D[i]);
+        rshift_sticky<NS, NU - 1>(q, nd);
+        BSFP_UNROLL
+        for (int i = 0; i < N1; ++i) sigf[i] = MUX(neg, q[2 + i], sig[i]);
+        gf = MUX(neg, q[1], g);
+        stf = MUX(neg, q[0], st);
+        BSFP_UNROLL
+        for (int i = 0; i < NU - 1; ++i) Df[i] = ANDN(D[i], neg);
+    }
+
+    /* step 5: rounding, specials, encoding */
+    W rup = W(0u);
+    if constexpr (!RZ) rup = F3<LUT_G_AND_LS>(gf, sigf[0], stf);
+    W mag[M + NU];
+    assemble<M, NU - 1>(Df, sigf, rup, mag);
+    const W zA = FTZ ? NOT(nzA) : NOT(OR(nzA, fA));
+    const W zB = FTZ ? NOT(nzB) : NOT(OR(nzB, fB));
+    const W infA = ANDN(aspec, fA), infB = ANDN(bspec, fB);
+    const W nan = OR(OR(AND(aspec, fA), AND(bspec, fB)), OR(AND(infA, infB), AND(zA, zB)));
+    const W spec = OR3(nan, infA, zB);
+    W zero = OR(zA, infB);
+    if constexpr (FTZ) zero = OR(zero, neg);
+    encode<E, M, NU, RZ, W, true>(mag, spec, nan, zero, s, W(0u), r);
+}
+
 /* ----------------------------------------------------------------- ops --- */
-enum Op : int { OP_ADD = 0, OP_SUB = 1, OP_MUL = 2, OP_FMA2 = 3 };
+enum Op : int { OP_ADD = 0, OP_SUB = 1, OP_MUL = 2, OP_FMA2 = 3, OP_DIV = 4 };
 
 /* Rounding mode of a format: bit 0 = toward zero (else to nearest even),
  * bit 1 = flush to zero (operands and results below the normal range are
@@ -623,7 +798,7 @@ enum Op : int { OP_ADD = 0, OP_SUB = 1, OP_MUL = 2, OP_FMA2 = 3 };
 BSFP_HDC constexpr bool mode_rz(int R) { return (R & 1) != 0; }
 BSFP_HDC constexpr bool mode_ftz(int R) { return (R & 2) != 0; }
 
-/* r = op(a, b[, c]); fma2 = add(mul(a, b), c), each rounded. */
+/* r = op(a, b[, c]); fma2 = add(mul(a, b), c), each rounded; div = a / b. */
 template <int E, int M, int R, int OP, class W>
 BSFP_HD void fp_op(const W* a, const W* b, const W* c, W* r) {
     constexpr bool RZ = mode_rz(R), FTZ = mode_ftz(R);
@@ -633,6 +808,8 @@ BSFP_HD void fp_op(const W* a, const W* b, const W* c, W* r) {
         fp_add<E, M, RZ, true, FTZ>(a, b, r);
     } else if constexpr (OP == OP_MUL) {
         fp_mul<E, M, RZ, FTZ>(a, b, r);
+    } else if constexpr (OP == OP_DIV) {
+        fp_div<E, M, RZ, FTZ>(a, b, r);
     } else {
         W p[1 + E + M];
         fp_mul<E, M, RZ, FTZ>(a, b, p);

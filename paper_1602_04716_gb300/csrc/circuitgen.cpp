@@ -19,7 +19,7 @@
  * For each format and rounding mode R (bit 0 toward zero, bit 1 flush to
  * zero) it prints GenCircuit<E, M, R, OPC>
  * specialisations for the op classes add (b's sign flip is applied by the
- * caller), mul and fma2, with eval(a, b, c, r) over the B slices of each
+ * caller), mul, fma2 and div, with eval(a, b, c, r) over the B slices of each
  * operand.  The printed file is included inside namespace bsfp by
  * gen_circuit.cuh, which defines BSFP_LOP3 and BSFP_GEN_FN.
  */
@@ -87,10 +87,11 @@ void emit(FILE* f, int opc) {
 
 template <int E, int M, int R>
 void emit_mode(FILE* f) {
-    /* op classes: 0 = add/sub, 1 = mul, 2 = fma2 (OpClass of binop.cuh) */
+    /* op classes: 0 = add/sub, 1 = mul, 2 = fma2, 3 = div (OpClass of binop.cuh) */
     emit<E, M, R, OP_ADD>(f, 0);
     emit<E, M, R, OP_MUL>(f, 1);
     emit<E, M, R, OP_FMA2>(f, 2);
+    emit<E, M, R, OP_DIV>(f, 3);
 }
 
 /* every rounding mode: RN, RZ, and both with flush to zero */

@@ -46,6 +46,7 @@ template <int E, int M> static long count_fmt(int rnd, int op) {
             case 1: return count_op<E, M, OP_SUB>(rnd);
             case 2: return count_op<E, M, OP_MUL>(rnd);
             case 3: return count_op<E, M, OP_FMA2>(rnd);
+            case 4: return count_op<E, M, OP_DIV>(rnd);
         }
         return -1;
     }
@@ -70,6 +71,6 @@ template <int E, int M> static long count_m(int m, int rnd, int op) {
 #define BSFP_GC_CAT(a, b) BSFP_GC_CAT2(a, b)
 
 extern "C" long BSFP_GC_CAT(bsfp_gate_count_e, BSFP_E)(int man_bits, int rnd, int op) {
-    if (man_bits < 1 || man_bits > 23 || op < 0 || op > 3 || rnd < 0 || rnd > 3) return -1;
+    if (man_bits < 1 || man_bits > 23 || op < 0 || op > 4 || rnd < 0 || rnd > 3) return -1;
     return bsfp::gc::count_m<BSFP_E, 1>(man_bits, rnd, op);
 }

@@ -109,6 +109,7 @@ bsfp_status run_op(int op, bsfp_format f, const uint32_t* a, const uint32_t* b, 
         case BSFP_OP_SUB: return bsfp_sub(f, a, b, out, n, s);
         case BSFP_OP_MUL: return bsfp_mul(f, a, b, out, n, s);
         case BSFP_OP_FMA2: return bsfp_fma2(f, a, b, c, out, n, s);
+        case BSFP_OP_DIV: return bsfp_div(f, a, b, out, n, s);
     }
     return BSFP_ERR_UNSUPPORTED;
 }

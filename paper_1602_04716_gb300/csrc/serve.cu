@@ -401,7 +401,7 @@ bsfp_status bsfp_server_submit(bsfp_server S, const bsfp_job* job, int64_t* id_o
     r.out_bytes = round_up((int64_t)(1 + job->f.exp_bits + job->f.man_bits) * r.S * 4, ARENA_ALIGN);
     if (r.own_out && r.out_bytes > S->opt.budget_bytes) return BSFP_ERR_BUDGET;
     r.opc = po.skip ? opclass(job->op) : po.opc;
-    r.kind = po.skip ? -1 : batch_kind(job->f.exp_bits, job->f.man_bits, job->f.rnd);
+    r.kind = (po.skip || r.opc >= OPC_COUNT) ? -1 : batch_kind(job->f.exp_bits, job->f.man_bits, job->f.rnd);
     const int64_t tile = 128LL * S->opt.wpt * BATCH_ROUNDS;
     r.tiles = (r.S + tile - 1) / tile;
     r.status = BSFP_OK;

@@ -45,6 +45,7 @@ static int dispatch_fmt(int rnd, int op, const uint32_t* a, const uint32_t* b, c
         case 1: return dispatch_mode<E, M, OP_SUB>(rnd, a, b, c, out, nwords, S);
         case 2: return dispatch_mode<E, M, OP_MUL>(rnd, a, b, c, out, nwords, S);
         case 3: return dispatch_mode<E, M, OP_FMA2>(rnd, a, b, c, out, nwords, S);
+        case 4: return dispatch_mode<E, M, OP_DIV>(rnd, a, b, c, out, nwords, S);
     }
     return -1;
 }

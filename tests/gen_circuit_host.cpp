@@ -35,12 +35,13 @@ static int run(bool neg_b, const uint32_t* a, const uint32_t* b, const uint32_t*
 template <int E, int M, int R>
 static int dispatch_opc(int op, const uint32_t* a, const uint32_t* b, const uint32_t* c, uint32_t* out, long nwords,
                         long S) {
-    /* op: 0 add, 1 sub, 2 mul, 3 fma2 -> op classes 0 (add/sub), 1, 2 */
+    /* op: 0 add, 1 sub, 2 mul, 3 fma2, 4 div -> op classes 0 (add/sub), 1, 2, 3 */
     switch (op) {
         case 0: return run<E, M, R, 0>(false, a, b, c, out, nwords, S);
         case 1: return run<E, M, R, 0>(true, a, b, c, out, nwords, S);
         case 2: return run<E, M, R, 1>(false, a, b, c, out, nwords, S);
         case 3: return run<E, M, R, 2>(false, a, b, c, out, nwords, S);
+        case 4: return run<E, M, R, 3>(false, a, b, c, out, nwords, S);
     }
     return -1;
 }

@@ -18,7 +18,7 @@ import synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_1602_04716_gb300", "csrc")
-OPS = ["add", "sub", "mul", "fma2"]
+OPS = ["add", "sub", "mul", "fma2", "div"]
 
 _L = None
 
@@ -87,7 +87,7 @@ MODES = [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ]
 
 
 @pytest.mark.parametrize("E,M", SMALL)
-@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 @pytest.mark.parametrize("rnd", MODES)
 def test_circuit_exhaustive_small(E, M, op, rnd):
     a, b = synth.all_pairs(1 + E + M)

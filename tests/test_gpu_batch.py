@@ -14,7 +14,7 @@ import paper_1602_04716_gb300 as bs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-OPS = ["add", "sub", "mul", "fma2"]
+OPS = ["add", "sub", "mul", "fma2", "div"]
 FTZ_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]
 
 
@@ -29,7 +29,7 @@ def _make_batch(njobs, seed, max_len=1 << 16, extra_formats=((6, 9), (3, 2), (8,
     jobs = []
     for i in range(njobs):
         E, M = fmts[int(r[4 * i] % len(fmts))]
-        op = OPS[int(r[4 * i + 1] % 4)]
+        op = OPS[int(r[4 * i + 1] % len(OPS))]
         # flush-to-zero modes where compiled (they run as plain kernels in a plan)
         rnd = int(r[4 * i + 2] % (4 if (E, M) in FTZ_FORMATS else 2))
         n = int(lens[i]) if i % 17 else (0 if i % 34 == 0 else int(lens[i]) + 31)

@@ -17,7 +17,7 @@ import paper_1602_04716_gb300 as bs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-OPS = ["add", "sub", "mul", "fma2"]
+OPS = ["add", "sub", "mul", "fma2", "div"]
 RNDS = [oracle.RN, oracle.RZ]
 
 
@@ -128,14 +128,14 @@ SMALL = [(2, 1), (2, 3), (3, 2), (3, 3), (2, 5), (3, 4), (4, 3), (5, 2)]
 @pytest.mark.parametrize("rnd", RNDS)
 def test_exhaustive_pairs_small_formats(E, M, rnd):
     a, b = synth.all_pairs(1 + E + M)
-    for op in ("add", "sub", "mul"):
+    for op in ("add", "sub", "mul", "div"):
         check(op, E, M, rnd, a, b)
 
 
 @pytest.mark.parametrize("rnd", RNDS)
 def test_exhaustive_pairs_1_4_4(rnd):
     a, b = synth.all_pairs(9)
-    for op in ("add", "sub", "mul"):
+    for op in ("add", "sub", "mul", "div"):
         check(op, 4, 4, rnd, a, b)
 
 
@@ -188,7 +188,7 @@ FTZ_MODES = [oracle.RN_FTZ, oracle.RZ_FTZ]
 @pytest.mark.parametrize("rnd", FTZ_MODES)
 def test_flush_to_zero_exhaustive_1_4_3(rnd):
     a, b = synth.all_pairs(8)
-    for op in ("add", "sub", "mul"):
+    for op in ("add", "sub", "mul", "div"):
         check(op, 4, 3, rnd, a, b)
     i = np.arange(1 << 24, dtype=np.uint32)
     check("fma2", 4, 3, rnd, i >> 16, (i >> 8) & 255, i & 255)

@@ -37,14 +37,14 @@ def test_pipeline_matches_oracle(E, M, pinned):
         for rnd in (0, 1):
             f = bs.Format(E, M, rnd)
             a, b, c = (_host(E, M, n, 100 * n + s, pinned) for s in (1, 2, 3))
-            ops = ["add", "sub", "mul", "fma2"]
-            outs = [_host(E, M, n, 0, pinned) for _ in ops]
-            pipe.run(f, ops, a, b, outs, n, c=c)
             av, bv, cv = (_np(x, dt).astype(np.uint32) for x in (a, b, c))
-            for op, o in zip(ops, outs):
-                want = oracle.binop(op, E, M, rnd, av, bv, cv)
-                got = _np(o, dt).astype(np.uint32)
-                assert (got == want).all(), "%s 1/%d/%d rnd=%d n=%d" % (op, E, M, rnd, n)
+            for ops in (["add", "sub", "mul", "fma2"], ["div"]):
+                outs = [_host(E, M, n, 0, pinned) for _ in ops]
+                pipe.run(f, ops, a, b, outs, n, c=c)
+                for op, o in zip(ops, outs):
+                    want = oracle.binop(op, E, M, rnd, av, bv, cv)
+                    got = _np(o, dt).astype(np.uint32)
+                    assert (got == want).all(), "%s 1/%d/%d rnd=%d n=%d" % (op, E, M, rnd, n)
     pipe.close()
 
 

@@ -13,7 +13,7 @@ import paper_1602_04716_gb300 as bs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-OPS = ["add", "sub", "mul", "fma2"]
+OPS = ["add", "sub", "mul", "fma2", "div"]
 
 
 def _dev(x):
@@ -27,7 +27,7 @@ def _requests(nreq, seed, lo=1, hi=1 << 16, fmts=None):
     reqs = []
     for i in range(nreq):
         E, M = fmts[int(r[3 * i] % len(fmts))]
-        op = OPS[int(r[3 * i + 1] % 4)]
+        op = OPS[int(r[3 * i + 1] % len(OPS))]
         rnd = int(r[3 * i + 2] % 2)
         n = 0 if i % 37 == 3 else int(lens[i])
         B = 1 + E + M

@@ -24,7 +24,7 @@ from paper_1602_04716_gb300 import bsfp as _binding  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-OPS = ["add", "sub", "mul", "fma2"]
+OPS = ["add", "sub", "mul", "fma2", "div"]
 
 
 def _batch(njobs, seed, max_len):
@@ -36,7 +36,7 @@ def _batch(njobs, seed, max_len):
     specs, keep = [], []
     for i in range(njobs):
         E, M = fmts[int(r[3 * i] % len(fmts))]
-        op = OPS[int(r[3 * i + 1] % 4)]
+        op = OPS[int(r[3 * i + 1] % len(OPS))]
         f = bs.Format(E, M, int(r[3 * i + 2] % 2))
         n = 0 if i % 29 == 5 else int(lens[i])
         ops_ = []
