@@ -361,6 +361,7 @@ def run_gpu(args):
 BATCH_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
 FTZ_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]   # compiled with flush to zero too
 MODE_NAMES = ["RN", "RZ", "RN_FTZ", "RZ_FTZ"]
+SWEEP_OPS = ("add", "mul", "fma2", "div")
 
 
 def batched_workload(bs, torch, njobs, lo, hi, seed, rank=0, formats=BATCH_FORMATS, ops=("add", "mul")):
@@ -532,7 +533,7 @@ def run_small_case(bs, torch, rank):
 
 def run_sweep(bs, torch, args, rank, hbm, L):
     """Format sweep: every 1/E/M with E in 3..8 and M in 2..23, n elements,
-    bs_add, bs_mul and fma2 under RN and RZ (and both with flush to zero for
+    bs_add, bs_mul, fma2 and bs_div under RN and RZ (and both with flush to zero for
     the formats compiled with it), operands from the same value
     recipe.  Per launch: CUDA-event time (median of 3 after one warm-up), HBM
     GB/s of the algorithmic bytes, logic-op rate from the gate count, and the
@@ -557,7 +558,7 @@ def run_sweep(bs, torch, args, rank, hbm, L):
             modes = (0, 1, 2, 3) if (E, M) in FTZ_FORMATS else (0, 1)
             for rnd in modes:
                 f = bs.Format(E, M, rnd)
-                for op in ("add", "mul", "fma2"):
+                for op in SWEEP_OPS:
                     ts = []
                     for k in range(4):
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -580,13 +581,13 @@ def run_sweep(bs, torch, args, rank, hbm, L):
             del ops_, out, std
     summary = {"formats": len({r["fmt"] for r in rows}), "elements": n}
     for rnd in ("RN", "RZ"):
-        for op in ("add", "mul", "fma2"):
+        for op in SWEEP_OPS:
             sel = [r for r in rows if r["op"] == op and r["rnd"] == rnd]
             fr = np.array([r["frac"] for r in sel])
             summary["%s_%s" % (op, rnd)] = {"frac_min": float(fr.min()), "frac_median": float(np.median(fr)),
                                             "frac_max": float(fr.max()),
                                             "alu_bound_formats": sum(1 for r in sel if r["bound"] == "alu")}
-    for op in ("add", "mul", "fma2"):
+    for op in SWEEP_OPS:
         rn = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN"}
         rz = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RZ"}
         tr = np.array([rz[k]["ms"] / rn[k]["ms"] for k in rn])
@@ -594,7 +595,7 @@ def run_sweep(bs, torch, args, rank, hbm, L):
         summary["rz_over_rn_%s" % op] = {"time_median": float(np.median(tr)), "time_min": float(tr.min()),
                                          "gates_median": float(np.median(gr)), "gates_min": float(gr.min())}
     # flush to zero against gradual underflow, on the formats compiled with it
-    for op in ("add", "mul", "fma2"):
+    for op in SWEEP_OPS:
         pl = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN"}
         fz = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN_FTZ"}
         summary["ftz_over_rn_%s" % op] = {k: {"time": fz[k]["ms"] / pl[k]["ms"],

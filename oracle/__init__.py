@@ -63,6 +63,10 @@ def lib():
             L.oracle_fma2_1.restype = u32
             L.oracle_binop.argtypes = [i32, i32, i32, i32, p, p, p, p, i64]
             L.oracle_binop.restype = None
+            for name in ("oracle_from_f32", "oracle_to_f32"):
+                fn = getattr(L, name)
+                fn.argtypes = [i32, i32, i32, p, p, i64]
+                fn.restype = None
             L.oracle_plane_stride.argtypes = [i64]
             L.oracle_plane_stride.restype = i64
             L.oracle_pack.argtypes = [i32, p, i64, p, i64]
@@ -111,6 +115,22 @@ def div(E, M, rnd, a, b):
 
 def fma2(E, M, rnd, a, b, c):
     return binop("fma2", E, M, rnd, a, b, c)
+
+
+def from_f32(E: int, M: int, rnd: int, x) -> np.ndarray:
+    """binary32 bit patterns -> 1/E/M encodings, one rounding in mode rnd."""
+    x = _u32(x)
+    out = np.empty_like(x)
+    lib().oracle_from_f32(E, M, rnd, _ptr(x), _ptr(out), x.size)
+    return out
+
+
+def to_f32(E: int, M: int, rnd: int, x) -> np.ndarray:
+    """1/E/M encodings -> binary32 bit patterns (exact; NaN canonical)."""
+    x = _u32(x)
+    out = np.empty_like(x)
+    lib().oracle_to_f32(E, M, rnd, _ptr(x), _ptr(out), x.size)
+    return out
 
 
 def plane_stride(n: int) -> int:

@@ -172,6 +172,13 @@ class Format:
             return s * self.sign_bit
         return self.round(vx / vy, rnd)
 
+    def from_value(self, v, s: int, rnd: int) -> int:
+        """Encoding of an exact value v (a Fraction; s its sign, for zero)
+        rounded in mode rnd: the conversion of another format's value."""
+        if v == 0:
+            return s * self.sign_bit
+        return self.round(v, rnd)
+
     def fma2(self, x: int, y: int, z: int, rnd: int) -> int:
         return self.add(self.mul(x, y, rnd), z, rnd)
 

@@ -329,6 +329,45 @@ void oracle_binop(int op, int E, int M, int rz, const uint32_t *a, const uint32_
     }
 }
 
+/* Conversion from IEEE binary32 (the paper's FP32, Sec. 5.2) to 1/E/M: the
+ * exact value of the binary32 encoding, rounded once in the target's mode
+ * (NaN -> the canonical NaN, infinities and zeros keep their sign).  A
+ * binary32 subnormal is an ordinary (tiny) value here; under flush to zero
+ * it becomes a zero like any other tiny result. */
+static uint32_t o_from_f32(const fmt_t *f, uint32_t x) {
+    fmt_t f32 = mkfmt(8, 23, 0);
+    val_t v = decode(&f32, x);
+    if (v.cls == CLS_NAN) return canonical_nan(f);
+    if (v.cls == CLS_INF) return infinity(f, v.s);
+    if (v.mant == 0) return enc(f, v.s, 0, 0);
+    big T; big_from_u64(&T, v.mant);
+    return round_encode(f, v.s, &T, v.q);
+}
+
+/* Conversion from 1/E/M to binary32: exact (E <= 8, M <= 23), operands read
+ * under the format's mode (flush to zero reads exponent field 0 as zero). */
+static uint32_t o_to_f32(const fmt_t *f, uint32_t x) {
+    fmt_t f32 = mkfmt(8, 23, 0);
+    val_t v = decode(f, x);
+    if (v.cls == CLS_NAN) return canonical_nan(&f32);
+    if (v.cls == CLS_INF) return infinity(&f32, v.s);
+    if (v.mant == 0) return enc(&f32, v.s, 0, 0);
+    big T; big_from_u64(&T, v.mant);
+    return round_encode(&f32, v.s, &T, v.q);
+}
+
+void oracle_from_f32(int E, int M, int mode, const uint32_t *x, uint32_t *out, int64_t n) {
+    fmt_t f = mkfmt(E, M, mode);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) out[i] = o_from_f32(&f, x[i]);
+}
+
+void oracle_to_f32(int E, int M, int mode, const uint32_t *x, uint32_t *out, int64_t n) {
+    fmt_t f = mkfmt(E, M, mode);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) out[i] = o_to_f32(&f, x[i]);
+}
+
 /* Bitslice plane stride in 32-bit words: ceil(n/32) rounded up to 32 words. */
 int64_t oracle_plane_stride(int64_t n) {
     int64_t words = (n + 31) / 32;

@@ -397,3 +397,98 @@ def test_invariants(E, M, rnd):
     assert np.array_equal(m2[ok], (m1 ^ sb)[ok])
     assert np.array_equal(sub(x, y), add(x, y ^ sb))
     assert B <= 32
+
+
+# ---------------------------------------------------------------------------
+# conversions binary32 <-> 1/E/M
+# ---------------------------------------------------------------------------
+def _f32_operands(n=1 << 16, seed=81):
+    """Uniform binary32 patterns, values near every target's range (exponent
+    fields 100..140 cover the normal ranges of 1/5/M and their edges), the
+    binary32 subnormals, and the specials."""
+    r = synth.splitmix64(seed, 3 * n)
+    u = r[:n].astype(np.uint32)
+    mid = ((r[n:2 * n] & np.uint64(0x807FFFFF)) | ((np.uint64(100) + r[2 * n:] % np.uint64(41)) << np.uint64(23)))
+    sub = (r[2 * n:] & np.uint64(0x807FFFFF)).astype(np.uint32)
+    spec = np.array([0, 0x80000000, 0x7F800000, 0xFF800000, 0x7FC00000, 0x7F800001, 0xFFFFFFFF, 0x00000001,
+                     0x007FFFFF, 0x00800000, 0x7F7FFFFF, 0x3F800000, 0x477FE000, 0x477FF000, 0x477FF001,
+                     0x38800000, 0x387FC000, 0x33800000, 0x33000000, 0x33000001], np.uint32)
+    return np.concatenate([u, mid.astype(np.uint32), sub, spec])
+
+
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ])
+def test_from_f32_binary16_vs_numpy(rnd):
+    """1/5/10 from binary32: numpy's binary32 -> binary16 cast rounds to
+    nearest even; stepping it one place toward zero when it went away from
+    zero gives round toward zero."""
+    x = _f32_operands()
+    f = x.view(np.float32)
+    with np.errstate(all="ignore"):
+        h = f.astype(np.float16)
+        if rnd == oracle.RZ:
+            away = np.abs(h.astype(np.float32)) > np.abs(f)
+            h = np.where(away, np.nextafter(h, np.float16(0)), h)
+    want = h.view(np.uint16).astype(np.uint32)
+    got = oracle.from_f32(5, 10, rnd, x)
+    ok = H.nan_class_equal(5, 10, got, want)
+    assert ok.all(), "first mismatch %#x got %#x want %#x" % (x[~ok][0], got[~ok][0], want[~ok][0])
+
+
+def test_from_f32_bfloat16_vs_torch():
+    torch = pytest.importorskip("torch")
+    x = _f32_operands()
+    t = torch.from_numpy(x.view(np.float32).copy()).to(torch.bfloat16)
+    want = t.view(torch.int16).numpy().astype(np.uint16).astype(np.uint32)
+    got = oracle.from_f32(8, 7, oracle.RN, x)
+    ok = H.nan_class_equal(8, 7, got, want)
+    assert ok.all(), "first mismatch %#x got %#x want %#x" % (x[~ok][0], got[~ok][0], want[~ok][0])
+
+
+def test_from_f32_binary32_is_the_identity():
+    x = _f32_operands()
+    for rnd in (oracle.RN, oracle.RZ):
+        got = oracle.from_f32(8, 23, rnd, x)
+        ok = H.nan_class_equal(8, 23, got, x)
+        assert ok.all()
+
+
+@pytest.mark.parametrize("E,M", [(2, 1), (3, 2), (4, 3), (5, 2), (3, 4)])
+@pytest.mark.parametrize("rnd", [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ])
+def test_from_f32_vs_bruteforce(E, M, rnd):
+    F = bf.fmt(E, M)
+    x = _f32_operands(1 << 12, 90 + E * 8 + M)
+    got = oracle.from_f32(E, M, rnd, x)
+    for xi, gi in zip(x, got):
+        s, e, fr = (int(xi) >> 31) & 1, (int(xi) >> 23) & 255, int(xi) & 0x7FFFFF
+        if e == 255:
+            want = F.nan if fr else F.inf(s)
+        else:
+            v = Fraction(fr if e == 0 else fr + (1 << 23), 1 << 23) * Fraction(2) ** ((e if e else 1) - 127)
+            want = F.from_value(-v if s else v, s, rnd)
+        assert int(gi) == want, "x=%#x got %#x want %#x" % (xi, gi, want)
+
+
+def test_to_f32_vs_host_casts():
+    """1/5/10 and 1/8/7 widen exactly to binary32 through numpy / torch."""
+    torch = pytest.importorskip("torch")
+    h = np.arange(1 << 16, dtype=np.uint32)
+    want = h.astype(np.uint16).view(np.float16).astype(np.float32).view(np.uint32)
+    got = oracle.to_f32(5, 10, oracle.RN, h)
+    assert H.nan_class_equal(8, 23, got, want).all()
+    t = torch.from_numpy(h.astype(np.uint16).view(np.int16).copy()).view(torch.bfloat16).to(torch.float32)
+    want = t.view(torch.int32).numpy().view(np.uint32)
+    got = oracle.to_f32(8, 7, oracle.RN, h)
+    assert H.nan_class_equal(8, 23, got, want).all()
+
+
+@pytest.mark.parametrize("E,M", [(2, 1), (3, 2), (4, 3), (6, 9), (7, 13)])
+def test_to_f32_round_trips(E, M):
+    """Every value of 1/E/M is a binary32 value: converting it to binary32 and
+    back (either rounding) returns it, NaNs as the canonical NaN."""
+    B = 1 + E + M
+    x = (np.arange(1 << B, dtype=np.uint32) if B <= 16 else synth.uniform_bits(B, 1 << 16, 3).astype(np.uint32))
+    for rnd in (oracle.RN, oracle.RZ):
+        back = oracle.from_f32(E, M, rnd, oracle.to_f32(E, M, rnd, x))
+        assert H.nan_class_equal(E, M, back, x).all()
+        nan = np.array([H.is_nan(E, M, v) for v in x])
+        assert (back[nan] == (((1 << E) - 1) << M | 1 << (M - 1))).all()
