@@ -330,6 +330,7 @@ def run_gpu(args):
         serving = run_serving(bs, torch, args, rank)
 
     small = run_small_case(bs, torch, rank) if args.sweep_n > 0 else None
+    conversions = run_conversions(bs, torch, n, hbm) if args.sweep_n > 0 else None
 
     sweep = None
     if args.sweep_n > 0:
@@ -350,7 +351,7 @@ def run_gpu(args):
                            "tuned_shapes_applied": tuned},
                 "roofline": roof, "kernels": kinfo, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
                 "cpu_baseline": cpu, "batched": batched, "serving": serving,
-                "format_sweep": sweep, "small_case": small}
+                "format_sweep": sweep, "small_case": small, "conversions": conversions}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -488,6 +489,46 @@ def run_serving(bs, torch, args, rank):
                        % (args.serve_rate, args.serve_seconds, args.serve_small_budget >> 20, args.serve_saturated,
                           ["1/%d/%d" % fm for fm in BATCH_FORMATS], pool, args.serve_slots))
     del keep
+    return out
+
+
+def run_conversions(bs, torch, n, hbm):
+    """bsfp_from_float (binary32 -> planes, RN), bsfp_to_float (planes ->
+    binary32), bsfp_pack and bsfp_unpack for the two formats of the workload
+    at n elements: CUDA-event time (median of 5 after a warm-up) and
+    algorithmic GB/s (4 or the container bytes, + B/8 bytes per element)
+    against the measured copy bandwidth."""
+    stream = torch.cuda.current_stream()
+    src = torch.empty(n, dtype=torch.float32, device="cuda")
+    bs.bsfp_synth_fp_values(bs.Format(8, 23, 0), n, 2024, 0, 0, src)
+    back = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = {}
+    for E, M in FORMATS:
+        f = bs.Format(E, M, RND)
+        planes = bs.empty_bitslice(f, n)
+        std = bs.empty_standard(f, n)
+        cb = bs.bsfp_container_bytes(f)
+        for name, fn, bpe in (
+                ("from_float", lambda: bs.bsfp_from_float(f, src, n, planes, stream=stream), 4),
+                ("to_float", lambda: bs.bsfp_to_float(f, planes, n, back, stream=stream), 4),
+                ("pack", lambda: bs.bsfp_pack(f, std, n, planes, stream=stream), cb),
+                ("unpack", lambda: bs.bsfp_unpack(f, planes, n, std, stream=stream), cb)):
+            fn()
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+            t = float(np.median(ts))
+            gbs = n * (bpe + (1 + E + M) / 8) / t / 1e9
+            out["%s 1/%d/%d" % (name, E, M)] = {"ms": t * 1e3, "elements_per_s": n / t, "hbm_gbs": gbs,
+                                                "hbm_frac": gbs / hbm}
+        del planes, std
+    out["workload"] = ("binary32 values of the workload recipe (1/8/23), %d elements, RN; pack/unpack of the "
+                       "standard representation beside them" % n)
     return out
 
 

@@ -103,6 +103,29 @@ bsfp_status bsfp_pack(bsfp_format f, const void* std_in, int64_t n, uint32_t* bs
 /* unpack: the inverse of pack; writes exactly n containers of std_out. */
 bsfp_status bsfp_unpack(bsfp_format f, const uint32_t* bs_in, int64_t n, void* std_out, bsfp_stream_t s);
 
+/* --------------------------------------------------------- conversions --- */
+/* Native floats <-> bitslice operands, fused with the transpose (not among
+ * the paper's operations, whose inputs are already in the format: the step
+ * before and after them for data held as ordinary floats).  Each is one
+ * kernel: the values are transposed into slices in the warp and converted by
+ * a logic circuit over whole words, like the ops. */
+typedef enum { BSFP_FLOAT32 = 0, BSFP_BFLOAT16 = 1, BSFP_FLOAT16 = 2 } bsfp_float_type;
+
+/* bs_out (B planes of stride bsfp_plane_stride(n)) = in[n] converted to
+ * format f: the exact value of each IEEE binary32 / bfloat16 / binary16
+ * element (type), rounded once in f's mode (RN or RZ, flush to zero with
+ * the _FTZ modes); NaN becomes the canonical NaN, overflow follows f's
+ * rounding (Inf for RN, the largest finite value for RZ).  in aligned to its
+ * element size, bs_out to 16 bytes; padding written as zero.  Errors: as
+ * bsfp_pack; an unknown type returns BSFP_ERR_UNSUPPORTED. */
+bsfp_status bsfp_from_float(bsfp_format f, int32_t type, const void* in, int64_t n, uint32_t* bs_out,
+                            bsfp_stream_t s);
+/* out[n] (IEEE binary32) = the elements of bs_in, exactly (every value of a
+ * format with E <= 8 and M <= 23 is a binary32 value); NaN becomes the
+ * canonical binary32 NaN 0x7FC00000; with an _FTZ mode an element whose
+ * exponent field is 0 reads as a zero of its sign.  out aligned to 4 bytes. */
+bsfp_status bsfp_to_float(bsfp_format f, const uint32_t* bs_in, int64_t n, float* out, bsfp_stream_t s);
+
 /* ------------------------------------------------------------------ ops --- */
 /* out = a + b, element-wise, one rounding (Sec. 4, Table 1 row Add/Sub). */
 bsfp_status bsfp_add(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,

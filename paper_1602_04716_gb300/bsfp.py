@@ -111,6 +111,8 @@ def _lib():
                 "bsfp_mul": (i32, [F, p, p, p, i64, p]),
                 "bsfp_fma2": (i32, [F, p, p, p, p, i64, p]),
                 "bsfp_div": (i32, [F, p, p, p, i64, p]),
+                "bsfp_from_float": (i32, [F, i32, p, i64, p, p]),
+                "bsfp_to_float": (i32, [F, p, i64, p, p]),
                 "bsfp_status_str": (ctypes.c_char_p, [i32]),
                 "bsfp_last_cuda_error": (i32, []),
                 "bsfp_gate_count": (i64, [F, i32]),
@@ -230,6 +232,28 @@ def bsfp_op(op: str, f, a, b, out, n: int, c=None, stream=None):
     if op == "fma2":
         return bsfp_fma2(f, a, b, c, out, n, stream)
     return {"add": bsfp_add, "sub": bsfp_sub, "mul": bsfp_mul, "div": bsfp_div}[op](f, a, b, out, n, stream)
+
+
+# ---------------------------------------------------------- conversions ---
+FLOAT32, BFLOAT16, FLOAT16 = 0, 1, 2
+
+
+def float_type_of(t) -> int:
+    """bsfp_float_type of a torch tensor (float32, bfloat16 or float16)."""
+    import torch
+    return {torch.float32: FLOAT32, torch.bfloat16: BFLOAT16, torch.float16: FLOAT16}[t.dtype]
+
+
+def bsfp_from_float(f, src, n: int, bs_out, src_type=None, stream=None):
+    """Native floats (a device tensor of float32 / bfloat16 / float16, or a
+    pointer with src_type) -> bitslice planes of format f, rounded once."""
+    t = float_type_of(src) if src_type is None else src_type
+    _check(_lib().bsfp_from_float(_fmt(f), t, _ptr(src), n, _ptr(bs_out), _stream(stream)), "bsfp_from_float")
+
+
+def bsfp_to_float(f, bs_in, n: int, out, stream=None):
+    """Bitslice planes of format f -> float32 (exact)."""
+    _check(_lib().bsfp_to_float(_fmt(f), _ptr(bs_in), n, _ptr(out), _stream(stream)), "bsfp_to_float")
 
 
 # ---------------------------------------------------------- diagnostics ---

@@ -18,11 +18,13 @@
 
 #include "binop.cuh"
 #include "bsfp.h"
+#include "convert.cuh"
 #include "internal.h"
 
 namespace bsfp {
 
 BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_ALL];
+ConvEntry g_conv_table[9][24][4];
 
 /* Each exponent width is compiled as two translation units, M in [1, 11]
  * and [12, 23]; each fills its part of the table. */
@@ -30,6 +32,8 @@ BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_ALL];
 BSFP_DECL_REG(2) BSFP_DECL_REG(3) BSFP_DECL_REG(4) BSFP_DECL_REG(5) BSFP_DECL_REG(6) BSFP_DECL_REG(7)
 BSFP_DECL_REG(8)
 #undef BSFP_DECL_REG
+void register_conv_e2(); void register_conv_e3(); void register_conv_e4(); void register_conv_e5();
+void register_conv_e6(); void register_conv_e7(); void register_conv_e8();
 
 cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st);
 cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st);
@@ -43,6 +47,8 @@ static void init_tables() {
     register_e6_m1(); register_e6_m12();
     register_e7_m1(); register_e7_m12();
     register_e8_m1(); register_e8_m12();
+    register_conv_e2(); register_conv_e3(); register_conv_e4(); register_conv_e5();
+    register_conv_e6(); register_conv_e7(); register_conv_e8();
 }
 
 /* Launch shape per (E, M, rounding, op class): words per thread and resident
@@ -237,6 +243,49 @@ bsfp_status bsfp_fma2(bsfp_format f, const uint32_t* a, const uint32_t* b, const
 
 bsfp_status bsfp_div(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n, bsfp_stream_t s) {
     return run_binop(f, BSFP_OP_DIV, a, b, nullptr, out, n, (cudaStream_t)s);
+}
+
+/* Grid of the conversions: the word-column tiles over 4-warp blocks, at most
+ * 8 blocks per SM. */
+static int conv_grid(int64_t tiles) {
+    const int64_t want = (tiles + CV_WARPS - 1) / CV_WARPS;
+    const int64_t cap = (int64_t)device_num_sms() * 8;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+bsfp_status bsfp_from_float(bsfp_format f, int32_t type, const void* in, int64_t n, uint32_t* bs_out,
+                            bsfp_stream_t s) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    if (type < BSFP_FLOAT32 || type > BSFP_FLOAT16) return BSFP_ERR_UNSUPPORTED;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    if (!in || !bs_out) return BSFP_ERR_NULL;
+    if (!aligned(in, type == BSFP_FLOAT32 ? 4 : 2) || !aligned(bs_out, 16)) return BSFP_ERR_ALIGN;
+    std::call_once(g_init_once, init_tables);
+    const ConvEntry& e = g_conv_table[f.exp_bits][f.man_bits][f.rnd];
+    if (!e.from) return BSFP_ERR_UNSUPPORTED;
+    const int64_t S = bsfp_plane_stride(n);
+    const cudaError_t err = e.from(in, type, n, bs_out, S, conv_grid(S / 32), (cudaStream_t)s);
+    if (err != cudaSuccess) return cuda_fail(err);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+bsfp_status bsfp_to_float(bsfp_format f, const uint32_t* bs_in, int64_t n, float* out, bsfp_stream_t s) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    if (!bs_in || !out) return BSFP_ERR_NULL;
+    if (!aligned(bs_in, 16) || !aligned(out, 4)) return BSFP_ERR_ALIGN;
+    std::call_once(g_init_once, init_tables);
+    const ConvEntry& e = g_conv_table[f.exp_bits][f.man_bits][f.rnd];
+    if (!e.to) return BSFP_ERR_UNSUPPORTED;
+    const int64_t S = bsfp_plane_stride(n);
+    const cudaError_t err =
+        e.to(bs_in, S, n, reinterpret_cast<uint32_t*>(out), conv_grid((n + 1023) / 1024), (cudaStream_t)s);
+    if (err != cudaSuccess) return cuda_fail(err);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
 }
 
 const char* bsfp_status_str(int32_t status) {

@@ -789,6 +789,141 @@ template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void fp_div(
     encode<E, M, NU, RZ, W, true>(mag, spec, nan, zero, s, W(0u), r);
 }
 
+/* --------------------------------------------------------- conversions --- */
+/* r (1/E/M, B slices) = x (IEEE binary32, 32 slices: slice 0 the fraction's
+ * least significant bit, slice 31 the sign), rounded once in mode RZ/FTZ --
+ * a narrowing conversion built as a circuit over whole words like the ops.
+ * The binary32 exponent is rebiased, D = max(e,1) - 127 + bias - 1 (the
+ * target's exponent field minus one), the significand keeps its M+1 top
+ * bits with guard and sticky below, a target below the normal range takes
+ * the right shift into the subnormal positions, and rounding, overflow and
+ * the specials are those of the ops.  A binary32 subnormal is a tiny value
+ * like any other (flushed under FTZ). */
+template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void from_f32(const W* x, W* r) {
+    static_assert(E >= 2 && E <= 8 && M >= 1 && M <= 23, "narrowing from binary32 only");
+    constexpr int MS = 23, ES = 8;
+    constexpr int bias = (1 << (E - 1)) - 1;
+    constexpr int NU = 10;                         /* D lies in [-127, 253] */
+    const W s = x[31];
+    const W* ex = x + MS;
+    const W nz = or_n<ES>(ex);
+    const W spec = and_n<ES>(ex);
+    const W fx = or_n<MS>(x);
+    const W nan = AND(spec, fx);
+
+    /* D = max(e,1) + (bias - 128), NU-bit two's complement (a constant addend) */
+    constexpr uint32_t K = (uint32_t)(bias - 128) & ((1u << NU) - 1u);
+    W D[NU];
+    {
+        W c = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < NU; ++i) {
+            const W ai = (i == 0) ? OR(ex[0], NOT(nz)) : (i < ES ? ex[(i < ES) ? i : 0] : W(0u));
+            const bool k = (K >> i) & 1u;
+            D[i] = k ? NOT(XOR(ai, c)) : XOR(ai, c);
+            if (i + 1 < NU) c = k ? OR(ai, c) : AND(ai, c);
+        }
+    }
+    const W neg = D[NU - 1];
+
+    /* the target's M+1 significand bits, guard and sticky */
+    W sig[M + 1];
+    BSFP_UNROLL
+    for (int i = 0; i < M; ++i) sig[i] = x[MS - M + i];
+    sig[M] = nz;
+    const W g = (M < MS) ? x[(M < MS) ? MS - M - 1 : 0] : W(0u);
+    const W st = or_n<(M < MS - 1) ? MS - M - 1 : 0>(x);
+
+    W sigf[M + 1], Df[NU - 1];
+    W gf = g, stf = st;
+    if constexpr (FTZ) {
+        BSFP_UNROLL
+        for (int i = 0; i <= M; ++i) sigf[i] = sig[i];
+        BSFP_UNROLL
+        for (int i = 0; i < NU - 1; ++i) Df[i] = D[i];
+    } else {
+        constexpr int NQ = M + 3;
+        W q[NQ];
+        q[0] = OR(st, g);
+        BSFP_UNROLL
+        for (int p = 1; p <= M + 1; ++p) q[p] = sig[p - 1];
+        q[NQ - 1] = W(0u);
+        W nd[NU - 1];
+        BSFP_UNROLL
+        for (int i = 0; i < NU - 1; ++i) nd[i] = NOT(D[i]);
+        rshift_sticky<NQ, NU - 1>(q, nd);
+        BSFP_UNROLL
+        for (int i = 0; i <= M; ++i) sigf[i] = MUX(neg, q[2 + i], sig[i]);
+        gf = MUX(neg, q[1], g);
+        stf = MUX(neg, q[0], st);
+        BSFP_UNROLL
+        for (int i = 0; i < NU - 1; ++i) Df[i] = ANDN(D[i], neg);
+    }
+    W rup = W(0u);
+    if constexpr (!RZ) rup = F3<LUT_G_AND_LS>(gf, sigf[0], stf);
+    W mag[M + NU];
+    assemble<M, NU - 1>(Df, sigf, rup, mag);
+    W zero = NOT(OR(nz, fx));
+    if constexpr (FTZ) zero = OR3(zero, neg, NOT(nz));   /* tiny before rounding */
+    encode<E, M, NU, RZ, W, true>(mag, spec, nan, zero, s, W(0u), r);
+}
+
+/* r (IEEE binary32, 32 slices) = x (1/E/M), exactly: every value of a format
+ * with E <= 8 and M <= 23 is a binary32 value.  The significand (implicit bit
+ * included) is normalised left by the log shifter as far as the binary32
+ * exponent allows (subnormals of narrow-exponent formats become normal
+ * binary32 values); NaN becomes the canonical binary32 NaN.  Under FTZ an
+ * operand with exponent field 0 is a zero of its sign. */
+template <int E, int M, bool FTZ = false, class W> BSFP_HD void to_f32(const W* x, W* r) {
+    static_assert(E >= 2 && E <= 8 && M >= 1 && M <= 23, "widening to binary32 only");
+    constexpr int B = 1 + E + M;
+    constexpr int bias = (1 << (E - 1)) - 1;
+    const W s = x[B - 1];
+    const W* ex = x + M;
+    const W nz = or_n<E>(ex);
+    const W spec = and_n<E>(ex);
+    const W fx = or_n<M>(x);
+    const W nan = AND(spec, fx);
+
+    /* um1 = max(e,1) + (127 - bias) - 1: the binary32 exponent field of 1.f,
+     * minus one (8 bits; never above 253) */
+    constexpr uint32_t K = (uint32_t)(126 - bias);
+    W um1[8];
+    {
+        W c = W(0u);
+        BSFP_UNROLL
+        for (int i = 0; i < 8; ++i) {
+            const W ai = (i == 0) ? OR(ex[0], NOT(nz)) : (i < E ? ex[(i < E) ? i : 0] : W(0u));
+            const bool k = (K >> i) & 1u;
+            um1[i] = k ? NOT(XOR(ai, c)) : XOR(ai, c);
+            if (i + 1 < 8) c = k ? OR(ai, c) : AND(ai, c);
+        }
+    }
+    W sig[M + 1];
+    BSFP_UNROLL
+    for (int i = 0; i < M; ++i) sig[i] = x[i];
+    sig[M] = FTZ ? ~W(0u) : nz;
+    W D[8];
+    if constexpr (FTZ) {
+        BSFP_UNROLL
+        for (int i = 0; i < 8; ++i) D[i] = um1[i];
+    } else {
+        /* normalise by t = min(lz, um1), then D = um1 - t (>= 0) */
+        constexpr int KT = floor_log2(M);
+        W t[KT + 1];
+        lnorm<M + 1, 8>(sig, um1, t);
+        sub_un<8, KT + 1>(um1, t, D);
+    }
+    W mag8[M + 9];
+    assemble<M, 8>(D, sig, W(0u), mag8);
+    /* the binary32 magnitude: fraction bits M..1 at the top of the 23 */
+    W mag[23 + 9];
+    BSFP_UNROLL
+    for (int i = 0; i < 23 + 9; ++i) mag[i] = (i < 23 - M) ? W(0u) : mag8[(i < 23 - M) ? 0 : i - (23 - M)];
+    const W zero = FTZ ? NOT(nz) : NOT(OR(nz, fx));
+    encode<8, 23, 9, false, W, true>(mag, spec, nan, zero, s, W(0u), r);
+}
+
 /* ----------------------------------------------------------------- ops --- */
 enum Op : int { OP_ADD = 0, OP_SUB = 1, OP_MUL = 2, OP_FMA2 = 3, OP_DIV = 4 };
 

@@ -26,30 +26,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "warp_transpose.cuh"
+
 namespace bsfp {
 
 constexpr int TP_WARPS = 8;              /* warps per block */
 constexpr int TP_ROW = 33;               /* padded shared-memory row (words) */
-
-/* Transpose the 32x32 bit matrix held one row per lane: afterwards lane c
- * holds, in bit l, bit c of lane l's input row. */
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
-#pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
-        const uint32_t lowmask = (k == 16) ? 0x0000FFFFu
-                                 : (k == 8) ? 0x00FF00FFu
-                                 : (k == 4) ? 0x0F0F0F0Fu
-                                 : (k == 2) ? 0x33333333u : 0x55555555u;
-        const bool upper = (lane & k) != 0;
-        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, k);
-        /* rows without bit k take the partner's low columns moved up by k;
-         * rows with bit k take the partner's high columns moved down by k */
-        const uint32_t r = __funnelshift_l(y, y, upper ? 32 - k : k);
-        const uint32_t keep = upper ? ~lowmask : lowmask;
-        x = (x & keep) | (r & ~keep);
-    }
-    return x;
-}
 
 template <int CB> struct Container;
 template <> struct Container<1> { using T = uint8_t; };
@@ -69,16 +51,22 @@ __global__ void __launch_bounds__(32 * TP_WARPS) pack_kernel(const void* __restr
     const int64_t ntiles = S / 32;
     for (int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * TP_WARPS) {
         const int64_t e0 = tile * 1024;
-#pragma unroll 4
+        /* all loads of the tile first, so that they are in flight together */
+        uint32_t rows[32 / GP];
+#pragma unroll
         for (int t = 0; t < 32 / GP; ++t) {
             uint32_t row = 0;
 #pragma unroll
             for (int q = 0; q < GP; ++q) {
                 const int64_t i = e0 + (int64_t)(t * GP + q) * 32 + lane;
-                const uint32_t v = (i < n) ? (uint32_t)in[i] : 0u;
+                const uint32_t v = (i < n) ? (uint32_t)__ldcs(in + i) : 0u;
                 row |= v << (BITS * q);
             }
-            const uint32_t col = warp_transpose32(row, lane);
+            rows[t] = row;
+        }
+#pragma unroll
+        for (int t = 0; t < 32 / GP; ++t) {
+            const uint32_t col = warp_transpose32(rows[t], lane);
             /* lane = BITS*q + b now holds plane b of group t*GP+q */
             const int b = lane % BITS, g = t * GP + lane / BITS;
             if (b < B) s[b * TP_ROW + g] = col;

@@ -50,6 +50,34 @@ static int dispatch_fmt(int rnd, int op, const uint32_t* a, const uint32_t* b, c
     return -1;
 }
 
+template <int E, int M, int R>
+static void run_conv(int dir, const uint32_t* a, uint32_t* out, long nwords, long S) {
+    constexpr int B = 1 + E + M;
+    for (long w = 0; w < nwords; ++w) {
+        uint32_t x[32], r[32];
+        if (dir == 0) {   /* binary32 (32 planes) -> 1/E/M */
+            for (int i = 0; i < 32; ++i) x[i] = a[i * S + w];
+            from_f32<E, M, mode_rz(R), mode_ftz(R)>(x, r);
+            for (int i = 0; i < B; ++i) out[i * S + w] = r[i];
+        } else {          /* 1/E/M -> binary32 */
+            for (int i = 0; i < B; ++i) x[i] = a[i * S + w];
+            to_f32<E, M, mode_ftz(R)>(x, r);
+            for (int i = 0; i < 32; ++i) out[i * S + w] = r[i];
+        }
+    }
+}
+
+template <int E, int M>
+static int dispatch_conv(int rnd, int dir, const uint32_t* a, uint32_t* out, long nwords, long S) {
+    switch (rnd) {
+        case 0: run_conv<E, M, 0>(dir, a, out, nwords, S); return 0;
+        case 1: run_conv<E, M, 1>(dir, a, out, nwords, S); return 0;
+        case 2: run_conv<E, M, 2>(dir, a, out, nwords, S); return 0;
+        case 3: run_conv<E, M, 3>(dir, a, out, nwords, S); return 0;
+    }
+    return -1;
+}
+
 #define FMT(E, M) \
     if (e == E && m == M) return dispatch_fmt<E, M>(rnd, op, a, b, c, out, nwords, S);
 
@@ -59,5 +87,15 @@ extern "C" int host_circuit(int e, int m, int rnd, int op, const uint32_t* a, co
     FMT(2, 1) FMT(2, 3) FMT(3, 2) FMT(3, 3) FMT(2, 5) FMT(3, 4) FMT(4, 3) FMT(5, 2) FMT(4, 4) FMT(5, 4)
     FMT(4, 5) FMT(5, 7) FMT(5, 10) FMT(8, 7) FMT(8, 23) FMT(3, 23) FMT(8, 2) FMT(6, 9) FMT(7, 13)
     FMT(2, 23) FMT(8, 1) FMT(3, 12)
+    return -1;
+}
+
+#define FMTC(E, M) \
+    if (e == E && m == M) return dispatch_conv<E, M>(rnd, dir, a, out, nwords, S);
+
+/* dir 0: binary32 planes in (32 x S), 1/E/M planes out; dir 1: the reverse */
+extern "C" int host_convert(int e, int m, int rnd, int dir, const uint32_t* a, uint32_t* out, long nwords, long S) {
+    FMTC(2, 1) FMTC(3, 2) FMTC(4, 3) FMTC(5, 2) FMTC(3, 4) FMTC(4, 4) FMTC(5, 7) FMTC(5, 10) FMTC(8, 7)
+    FMTC(8, 23) FMTC(6, 9) FMTC(7, 13) FMTC(3, 23) FMTC(2, 23) FMTC(8, 1)
     return -1;
 }

@@ -169,3 +169,18 @@ def test_flush_to_zero_only_for_the_compiled_formats():
         assert L.bsfp_variants_compiled(bs.Format(6, 9, rnd), 2) == 0
         assert L.bsfp_variants_compiled(bs.Format(5, 7, rnd), 2) > 0
         assert bs.bsfp_gate_count(bs.Format(5, 7, rnd), "mul") < bs.bsfp_gate_count(bs.Format(5, 7, rnd & 1), "mul")
+
+
+def test_conversion_arguments_validated_before_any_cuda_call():
+    L = _binding._lib()
+    f = bs.Format(5, 7)
+    assert L.bsfp_from_float(f, 3, 256, 10, 256, None) == bs.ERR_UNSUPPORTED
+    assert L.bsfp_from_float(bs.Format(9, 7), 0, 256, 10, 256, None) == bs.ERR_FORMAT
+    assert L.bsfp_from_float(f, 0, None, 10, 256, None) == bs.ERR_NULL
+    assert L.bsfp_from_float(f, 0, 258, 10, 256, None) == bs.ERR_ALIGN
+    assert L.bsfp_from_float(f, 1, 258, 10, 260, None) == bs.ERR_ALIGN
+    assert L.bsfp_from_float(bs.Format(6, 9, bs.RN_FTZ), 0, 256, 10, 256, None) == bs.ERR_UNSUPPORTED
+    assert L.bsfp_from_float(f, 0, 256, -1, 256, None) == bs.ERR_SIZE
+    assert L.bsfp_from_float(f, 0, 256, 0, 256, None) == bs.OK
+    assert L.bsfp_to_float(f, 256, 10, 258, None) == bs.ERR_ALIGN
+    assert L.bsfp_to_float(bs.Format(6, 9, bs.RZ_FTZ), 256, 10, 256, None) == bs.ERR_UNSUPPORTED

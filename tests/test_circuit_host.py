@@ -32,6 +32,8 @@ def _lib():
         L = ctypes.CDLL(out)
         L.host_circuit.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 4 + [ctypes.c_long] * 2
         L.host_circuit.restype = ctypes.c_int
+        L.host_convert.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 2 + [ctypes.c_long] * 2
+        L.host_convert.restype = ctypes.c_int
         _L = L
     return _L
 
@@ -160,3 +162,42 @@ def test_generated_netlist_sampled(E, M, rnd):
             got = circuit(E, M, rnd, op, a, b, c, generated=True)
             want = oracle.binop(op, E, M, rnd, a, b, c)
             assert (got == want).all(), "%s %s: %s" % (gen, op, _first_bad(got, want, a, b, c))
+
+
+CONV = [(2, 1), (3, 2), (4, 3), (5, 2), (3, 4), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23), (6, 9), (7, 13), (3, 23),
+        (2, 23), (8, 1)]
+
+
+def convert(E, M, rnd, direction, x):
+    """direction 0: binary32 patterns -> 1/E/M; 1: 1/E/M -> binary32."""
+    B = 1 + E + M
+    x = np.asarray(x, np.uint32)
+    pin = oracle.pack(32 if direction == 0 else B, x)
+    S = pin.shape[1]
+    out = np.zeros((B if direction == 0 else 32, S), np.uint32)
+    rc = _lib().host_convert(E, M, rnd, direction, pin.ctypes.data, out.ctypes.data, S, S)
+    assert rc == 0
+    return oracle.unpack(B if direction == 0 else 32, out, x.size)
+
+
+def _f32_samples(n, seed):
+    r = synth.splitmix64(seed, 3 * n)
+    near = ((r[n:2 * n] & np.uint64(0x807FFFFF)) | ((np.uint64(96) + r[2 * n:] % np.uint64(48)) << np.uint64(23)))
+    spec = np.array([0, 0x80000000, 0x7F800000, 0xFF800000, 0x7FC00000, 0x7F800001, 0x00000001, 0x007FFFFF,
+                     0x00800000, 0x7F7FFFFF, 0x3F800000], np.uint32)
+    return np.concatenate([r[:n].astype(np.uint32), near.astype(np.uint32), (r[2 * n:] & np.uint64(0x807FFFFF))
+                           .astype(np.uint32), spec])
+
+
+@pytest.mark.parametrize("E,M", CONV)
+@pytest.mark.parametrize("rnd", MODES)
+def test_conversion_circuits(E, M, rnd):
+    x = _f32_samples(1 << 13, 300 + 32 * E + M)
+    got = convert(E, M, rnd, 0, x)
+    want = oracle.from_f32(E, M, rnd, x)
+    assert (got == want).all(), "from: " + _first_bad(got, want, x)
+    B = 1 + E + M
+    y = np.arange(1 << B, dtype=np.uint32) if B <= 14 else synth.uniform_bits(B, 1 << 14, 7).astype(np.uint32)
+    got = convert(E, M, rnd, 1, y)
+    want = oracle.to_f32(E, M, rnd, y)
+    assert (got == want).all(), "to: " + _first_bad(got, want, y)
