@@ -67,6 +67,8 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = [i32, i32, i32, p, p, i64]
                 fn.restype = None
+            L.oracle_int_binop.argtypes = [i32, i32, p, p, p, i64]
+            L.oracle_int_binop.restype = None
             L.oracle_plane_stride.argtypes = [i64]
             L.oracle_plane_stride.restype = i64
             L.oracle_pack.argtypes = [i32, p, i64, p, i64]
@@ -130,6 +132,18 @@ def to_f32(E: int, M: int, rnd: int, x) -> np.ndarray:
     x = _u32(x)
     out = np.empty_like(x)
     lib().oracle_to_f32(E, M, rnd, _ptr(x), _ptr(out), x.size)
+    return out
+
+
+INT_OPS = {"add": 0, "sub": 1, "mul": 2}
+
+
+def int_binop(op: str, w: int, a, b) -> np.ndarray:
+    """w-bit unsigned integer vectors (Sec. 3): op in {add, sub, mul}, the low
+    w bits of the exact result."""
+    a, b = _u32(a), _u32(b)
+    out = np.empty_like(a)
+    lib().oracle_int_binop(INT_OPS[op], w, _ptr(a), _ptr(b), _ptr(out), a.size)
     return out
 
 

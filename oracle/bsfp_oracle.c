@@ -368,6 +368,25 @@ void oracle_to_f32(int E, int M, int mode, const uint32_t *x, uint32_t *out, int
     for (int64_t i = 0; i < n; i++) out[i] = o_to_f32(&f, x[i]);
 }
 
+/* Integer bitslice vectors (Sec. 3, Fig. 2): elements are w-bit unsigned
+ * integers (1 <= w <= 32); add, sub and mul keep the low w bits of the exact
+ * result, i.e. arithmetic modulo 2^w (the carry out of the top slice is
+ * dropped, as in the Fig. 2 adder).  op: 0 add, 1 sub, 2 mul. */
+void oracle_int_binop(int op, int w, const uint32_t *a, const uint32_t *b, uint32_t *out, int64_t n) {
+    const uint64_t mask = (w >= 32) ? 0xFFFFFFFFull : ((1ull << w) - 1ull);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        const uint64_t x = a[i] & mask, y = b[i] & mask;
+        uint64_t r;
+        switch (op) {
+        case 0: r = x + y; break;
+        case 1: r = x + ((mask + 1ull) - y); break;   /* x - y modulo 2^w */
+        default: r = x * y; break;
+        }
+        out[i] = (uint32_t)(r & mask);
+    }
+}
+
 /* Bitslice plane stride in 32-bit words: ceil(n/32) rounded up to 32 words. */
 int64_t oracle_plane_stride(int64_t n) {
     int64_t words = (n + 31) / 32;

@@ -492,3 +492,39 @@ def test_to_f32_round_trips(E, M):
         assert H.nan_class_equal(E, M, back, x).all()
         nan = np.array([H.is_nan(E, M, v) for v in x])
         assert (back[nan] == (((1 << E) - 1) << M | 1 << (M - 1))).all()
+
+
+# ---------------------------------------------------------------------------
+# integer bitslice vectors (Sec. 3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("w,dt", [(8, np.uint8), (16, np.uint16), (32, np.uint32)])
+@pytest.mark.parametrize("op", ["add", "sub", "mul"])
+def test_int_ops_vs_numpy_wraparound(w, dt, op):
+    """At the machine widths the w-bit operations are numpy's unsigned
+    wrap-around arithmetic."""
+    n = 1 << 16
+    a = synth.uniform_bits(w, n, 111, 0).astype(np.uint32)
+    b = synth.uniform_bits(w, n, 111, 1).astype(np.uint32)
+    x, y = a.astype(dt), b.astype(dt)
+    with np.errstate(over="ignore"):
+        want = {"add": x + y, "sub": x - y, "mul": x * y}[op].astype(np.uint32)
+    assert (oracle.int_binop(op, w, a, b) == want).all()
+
+
+@pytest.mark.parametrize("w", [1, 2, 3, 5, 9, 13, 17, 23, 31])
+def test_int_ops_invariants(w):
+    """Ring laws modulo 2^w: commutativity, 0 and 1, a - a = 0, (a - b) + b = a,
+    distributivity, and 2^(w-1) * 2 = 0."""
+    n = 1 << 14
+    a, b, c = (synth.uniform_bits(w, n, 120 + w, k).astype(np.uint32) for k in range(3))
+    add = lambda x, y: oracle.int_binop("add", w, x, y)
+    sub = lambda x, y: oracle.int_binop("sub", w, x, y)
+    mul = lambda x, y: oracle.int_binop("mul", w, x, y)
+    zero, one = np.zeros_like(a), np.ones_like(a)
+    assert (add(a, b) == add(b, a)).all() and (mul(a, b) == mul(b, a)).all()
+    assert (add(a, zero) == a).all() and (mul(a, one) == a).all() and (mul(a, zero) == 0).all()
+    assert (sub(a, a) == 0).all() and (add(sub(a, b), b) == a).all()
+    assert (mul(a, add(b, c)) == add(mul(a, b), mul(a, c))).all()
+    top = np.full_like(a, 1 << (w - 1))
+    assert (mul(top, np.full_like(a, 2)) == 0).all()
+    assert (a < (1 << w)).all() and (add(a, b) < (1 << w)).all()
