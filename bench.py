@@ -331,6 +331,7 @@ def run_gpu(args):
 
     small = run_small_case(bs, torch, rank) if args.sweep_n > 0 else None
     conversions = run_conversions(bs, torch, n, hbm) if args.sweep_n > 0 else None
+    integers = run_integers(bs, torch, n, hbm, L) if args.sweep_n > 0 else None
 
     sweep = None
     if args.sweep_n > 0:
@@ -351,7 +352,8 @@ def run_gpu(args):
                            "tuned_shapes_applied": tuned},
                 "roofline": roof, "kernels": kinfo, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
                 "cpu_baseline": cpu, "batched": batched, "serving": serving,
-                "format_sweep": sweep, "small_case": small, "conversions": conversions}
+                "format_sweep": sweep, "small_case": small, "conversions": conversions,
+                "integers": integers}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -529,6 +531,43 @@ def run_conversions(bs, torch, n, hbm):
         del planes, std
     out["workload"] = ("binary32 values of the workload recipe (1/8/23), %d elements, RN; pack/unpack of the "
                        "standard representation beside them" % n)
+    return out
+
+
+def run_integers(bs, torch, n, hbm, L):
+    """Integer bitslice vectors (Sec. 3) at the widths the paper names (5, 9,
+    13 and 17 bits): add and mul modulo 2^w on n-element vectors of uniform
+    w-bit values; CUDA-event time (median of 5), GB/s of the algorithmic
+    bytes (3w/8 per element) and the roofline fraction."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for w in (5, 9, 13, 17):
+        # uniform random plane words are uniform random w-bit elements
+        words = w * bs.bsfp_plane_stride(n)
+        gen = torch.Generator(device="cuda").manual_seed(1602 + w)
+        ops_ = [torch.randint(-2 ** 31, 2 ** 31 - 1, (words,), dtype=torch.int32, device="cuda", generator=gen)
+                for _ in range(2)]
+        res = torch.empty(words, dtype=torch.int32, device="cuda")
+        for op in ("add", "mul"):
+            fn = lambda: bs.bsfp_int_op(op, w, ops_[0], ops_[1], res, n, stream=stream)
+            fn()
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+            t = float(np.median(ts))
+            G = bs.bsfp_int_gate_count(w, op)
+            bpe = 3 * w / 8
+            roof = min(hbm * 1e9 / bpe, L * 32 / G)
+            out["int%d_%s" % (w, op)] = {"ms": t * 1e3, "elements_per_s": n / t, "hbm_gbs": n * bpe / t / 1e9,
+                                         "gates_per_word": G, "frac": (n / t) / roof,
+                                         "bound": "hbm" if hbm * 1e9 / bpe <= L * 32 / G else "alu"}
+        del ops_, res
+    out["workload"] = "%d-element vectors of uniformly random w-bit integers, w in 5, 9, 13, 17" % n
     return out
 
 

@@ -148,6 +148,27 @@ bsfp_status bsfp_fma2(bsfp_format f, const uint32_t* a, const uint32_t* b, const
 bsfp_status bsfp_div(bsfp_format f, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
                      bsfp_stream_t s);
 
+/* ----------------------------------------------------- integer vectors --- */
+/* Integer bitslice vectors (Sec. 3, Fig. 2): elements are w-bit unsigned
+ * integers, 1 <= w <= 32 ("vectors of numbers with 5, 9, or 13 bits"), in the
+ * bitslice layout above with B = w planes; the standard representation is
+ * the w-bit value right-aligned in a uint8/16/32 container.  add, sub and mul
+ * return the low w bits of the exact result (arithmetic modulo 2^w, which is
+ * also two's-complement arithmetic); add is the Fig. 2 ripple-carry adder.
+ * Same pointer, alignment, n and error conventions as the float ops; a bad w
+ * returns BSFP_ERR_FORMAT. */
+bsfp_status bsfp_int_pack(int32_t bits, const void* std_in, int64_t n, uint32_t* bs_out, bsfp_stream_t s);
+bsfp_status bsfp_int_unpack(int32_t bits, const uint32_t* bs_in, int64_t n, void* std_out, bsfp_stream_t s);
+bsfp_status bsfp_int_add(int32_t bits, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                         bsfp_stream_t s);
+bsfp_status bsfp_int_sub(int32_t bits, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                         bsfp_stream_t s);
+bsfp_status bsfp_int_mul(int32_t bits, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                         bsfp_stream_t s);
+/* 3-input logic gates per 32-element word of the integer op (0 add, 1 sub,
+ * 2 mul) at width bits; -1 on bad arguments. */
+int64_t bsfp_int_gate_count(int32_t bits, int32_t op);
+
 /* -------------------------------------------------------------- batched --- */
 /* One element-wise op on one vector: the unit of a batch.  c is used by
  * BSFP_OP_FMA2 only.  Same pointer, alignment and n rules as the single ops. */

@@ -112,6 +112,12 @@ def _lib():
                 "bsfp_fma2": (i32, [F, p, p, p, p, i64, p]),
                 "bsfp_div": (i32, [F, p, p, p, i64, p]),
                 "bsfp_from_float": (i32, [F, i32, p, i64, p, p]),
+                "bsfp_int_pack": (i32, [i32, p, i64, p, p]),
+                "bsfp_int_unpack": (i32, [i32, p, i64, p, p]),
+                "bsfp_int_add": (i32, [i32, p, p, p, i64, p]),
+                "bsfp_int_sub": (i32, [i32, p, p, p, i64, p]),
+                "bsfp_int_mul": (i32, [i32, p, p, p, i64, p]),
+                "bsfp_int_gate_count": (i64, [i32, i32]),
                 "bsfp_to_float": (i32, [F, p, i64, p, p]),
                 "bsfp_status_str": (ctypes.c_char_p, [i32]),
                 "bsfp_last_cuda_error": (i32, []),
@@ -254,6 +260,33 @@ def bsfp_from_float(f, src, n: int, bs_out, src_type=None, stream=None):
 def bsfp_to_float(f, bs_in, n: int, out, stream=None):
     """Bitslice planes of format f -> float32 (exact)."""
     _check(_lib().bsfp_to_float(_fmt(f), _ptr(bs_in), n, _ptr(out), _stream(stream)), "bsfp_to_float")
+
+
+# ------------------------------------------------ integer vectors (Sec. 3) ---
+INT_OPS = {"add": 0, "sub": 1, "mul": 2}
+
+
+def bsfp_int_pack(bits: int, std_in, n: int, bs_out, stream=None):
+    _check(_lib().bsfp_int_pack(bits, _ptr(std_in), n, _ptr(bs_out), _stream(stream)), "bsfp_int_pack")
+
+
+def bsfp_int_unpack(bits: int, bs_in, n: int, std_out, stream=None):
+    _check(_lib().bsfp_int_unpack(bits, _ptr(bs_in), n, _ptr(std_out), _stream(stream)), "bsfp_int_unpack")
+
+
+def bsfp_int_op(op: str, bits: int, a, b, out, n: int, stream=None):
+    """w-bit integer vectors: op in {add, sub, mul}, modulo 2^bits."""
+    fn = {"add": _lib().bsfp_int_add, "sub": _lib().bsfp_int_sub, "mul": _lib().bsfp_int_mul}[op]
+    _check(fn(bits, _ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "bsfp_int_" + op)
+
+
+def bsfp_int_gate_count(bits: int, op) -> int:
+    return int(_lib().bsfp_int_gate_count(bits, INT_OPS.get(op, op)))
+
+
+def empty_int_bitslice(bits: int, n: int, device="cuda"):
+    import torch
+    return torch.empty(bits * bsfp_plane_stride(n), dtype=torch.int32, device=device)
 
 
 # ---------------------------------------------------------- diagnostics ---

@@ -51,6 +51,9 @@ def _units():
                       ["g++", "-std=c++17", "-O1", "-fPIC", "-I", CSRC, "-DBSFP_E=%d" % e, "-c",
                        os.path.join(CSRC, "gatecount.cpp")]))
         units.append(("conv_e%d.o" % e, cu + ["-DBSFP_E=%d" % e, os.path.join(CSRC, "conv_inst.cu")]))
+    for lo, hi in ((1, 16), (17, 32)):
+        units.append(("int_w%d.o" % lo, cu + ["-DBSFP_W_LO=%d" % lo, "-DBSFP_W_HI=%d" % hi,
+                                               os.path.join(CSRC, "int_ops.cu")]))
     for opc in range(3):
         units.append(("batch_opc%d.o" % opc, cu + ["-DBSFP_BATCH_OPC=%d" % opc, os.path.join(CSRC, "batch_inst.cu")]))
     for src in ("api.cu", "batch.cu", "batch_noalloc.cu", "serve.cu", "pipeline.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):

@@ -25,6 +25,9 @@ namespace bsfp {
 
 BinopEntry g_binop_table[TAB_E][TAB_M][TAB_R][OPC_ALL];
 ConvEntry g_conv_table[9][24][4];
+typedef cudaError_t (*int_launch_fn)(const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t S, int64_t nwords,
+                                     uint32_t tailmask, int grid, cudaStream_t s);
+int_launch_fn g_int_table[33][3];
 
 /* Each exponent width is compiled as two translation units, M in [1, 11]
  * and [12, 23]; each fills its part of the table. */
@@ -34,6 +37,7 @@ BSFP_DECL_REG(8)
 #undef BSFP_DECL_REG
 void register_conv_e2(); void register_conv_e3(); void register_conv_e4(); void register_conv_e5();
 void register_conv_e6(); void register_conv_e7(); void register_conv_e8();
+void register_int_w1(); void register_int_w17();
 
 cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st);
 cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st);
@@ -49,6 +53,7 @@ static void init_tables() {
     register_e8_m1(); register_e8_m12();
     register_conv_e2(); register_conv_e3(); register_conv_e4(); register_conv_e5();
     register_conv_e6(); register_conv_e7(); register_conv_e8();
+    register_int_w1(); register_int_w17();
 }
 
 /* Launch shape per (E, M, rounding, op class): words per thread and resident
@@ -287,6 +292,75 @@ bsfp_status bsfp_to_float(bsfp_format f, const uint32_t* bs_in, int64_t n, float
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return BSFP_OK;
 }
+
+/* ------------------------------------------------ integer vectors (Sec. 3) */
+static int int_container_bytes(int w) { return w <= 8 ? 1 : (w <= 16 ? 2 : 4); }
+
+bsfp_status bsfp_int_pack(int32_t bits, const void* std_in, int64_t n, uint32_t* bs_out, bsfp_stream_t s) {
+    if (bits < 1 || bits > 32) return BSFP_ERR_FORMAT;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    if (!std_in || !bs_out) return BSFP_ERR_NULL;
+    const int cb = int_container_bytes(bits);
+    if (!aligned(std_in, (uintptr_t)cb) || !aligned(bs_out, 16)) return BSFP_ERR_ALIGN;
+    const cudaError_t e = launch_pack(cb, std_in, n, bits, bs_out, bsfp_plane_stride(n), (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+bsfp_status bsfp_int_unpack(int32_t bits, const uint32_t* bs_in, int64_t n, void* std_out, bsfp_stream_t s) {
+    if (bits < 1 || bits > 32) return BSFP_ERR_FORMAT;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    if (!bs_in || !std_out) return BSFP_ERR_NULL;
+    const int cb = int_container_bytes(bits);
+    if (!aligned(bs_in, 16) || !aligned(std_out, (uintptr_t)cb)) return BSFP_ERR_ALIGN;
+    const cudaError_t e = launch_unpack(cb, bs_in, bsfp_plane_stride(n), bits, std_out, n, (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+static bsfp_status run_int(int32_t bits, int op, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                           bsfp_stream_t s) {
+    if (bits < 1 || bits > 32) return BSFP_ERR_FORMAT;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    if (!a || !b || !out) return BSFP_ERR_NULL;
+    if (!aligned(a, 16) || !aligned(b, 16) || !aligned(out, 16)) return BSFP_ERR_ALIGN;
+    std::call_once(g_init_once, init_tables);
+    const int_launch_fn fn = g_int_table[bits][op];
+    if (!fn) return BSFP_ERR_UNSUPPORTED;
+    const int64_t S = bsfp_plane_stride(n);
+    const int wpt = bits <= 16 ? 4 : 2;
+    const int64_t need = (S / wpt + 127) / 128;
+    const int64_t cap = (int64_t)device_num_sms() * 8;
+    const cudaError_t e = fn(a, b, out, S, (n + 31) / 32, (n % 32) ? ((1u << (n % 32)) - 1u) : ~0u,
+                             (int)(need < cap ? need : cap), (cudaStream_t)s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+bsfp_status bsfp_int_add(int32_t bits, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                         bsfp_stream_t s) {
+    return run_int(bits, IOP_ADD, a, b, out, n, s);
+}
+
+bsfp_status bsfp_int_sub(int32_t bits, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                         bsfp_stream_t s) {
+    return run_int(bits, IOP_SUB, a, b, out, n, s);
+}
+
+bsfp_status bsfp_int_mul(int32_t bits, const uint32_t* a, const uint32_t* b, uint32_t* out, int64_t n,
+                         bsfp_stream_t s) {
+    return run_int(bits, IOP_MUL, a, b, out, n, s);
+}
+
+long bsfp_int_gate_count_impl(int bits, int op);
+
+int64_t bsfp_int_gate_count(int32_t bits, int32_t op) { return bsfp_int_gate_count_impl(bits, op); }
 
 const char* bsfp_status_str(int32_t status) {
     switch (status) {

@@ -789,6 +789,70 @@ template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void fp_div(
     encode<E, M, NU, RZ, W, true>(mag, spec, nan, zero, s, W(0u), r);
 }
 
+/* ---------------------------------------------------- integer vectors --- */
+/* r = a + b (SUB: a - b = a + ~b + 1) modulo 2^w for w-bit unsigned (or
+ * two's-complement) integers: the ripple-carry adder of Sec. 3, Fig. 2, slice
+ * 0 first, one XOR3 and one MAJ per slice; the carry out of slice w-1 is
+ * dropped. */
+template <int w, bool SUB, class W> BSFP_HD void int_addsub(const W* a, const W* b, W* r) {
+    static_assert(w >= 1 && w <= 32, "1..32-bit integers");
+    /* slice 0: carry-in 0 (add) or 1 (sub) */
+    W c;
+    if constexpr (SUB) {
+        r[0] = XOR(a[0], b[0]);          /* a0 + ~b0 + 1 */
+        c = OR(a[0], NOT(b[0]));
+    } else {
+        r[0] = XOR(a[0], b[0]);
+        c = AND(a[0], b[0]);
+    }
+    BSFP_UNROLL
+    for (int i = 1; i < w; ++i) {
+        const W bi = SUB ? NOT(b[i]) : b[i];
+        r[i] = XOR3H(a[i], bi, c);
+        if (i + 1 < w) c = MAJH(a[i], bi, c);
+    }
+}
+
+/* r = a * b modulo 2^w: the carry-save array of the significand multiplier
+ * kept to the columns below w.  Row j adds the partial products a_i b_j of
+ * columns i + j < w; the carries of each row are absorbed by the next row's
+ * adders in the same columns and those of the last row leave the top column,
+ * so the low w sums are the product with no final adder. */
+template <int w, class W> BSFP_HD void int_mul(const W* a, const W* b, W* r) {
+    static_assert(w >= 1 && w <= 32, "1..32-bit integers");
+    W S[w], C[w + 1];
+    BSFP_UNROLL
+    for (int i = 0; i < w; ++i) S[i] = AND(a[i], b[0]);
+    BSFP_UNROLL
+    for (int j = 1; j < w; ++j) {
+        W nc[w + 1];
+        BSFP_UNROLL
+        for (int col = j; col < w; ++col) {
+            const W pp = AND(a[col - j], b[j]);
+            if (j == 1) {
+                nc[col + 1] = AND(S[col], pp);
+                S[col] = XOR(S[col], pp);
+            } else {
+                nc[col + 1] = MAJH(S[col], C[col], pp);
+                S[col] = XOR3H(S[col], C[col], pp);
+            }
+        }
+        BSFP_UNROLL
+        for (int col = j + 1; col < w; ++col) C[col] = nc[col];
+    }
+    BSFP_UNROLL
+    for (int i = 0; i < w; ++i) r[i] = S[i];
+}
+
+/* integer op codes (bsfp_int_* in bsfp.h) */
+enum IntOp : int { IOP_ADD = 0, IOP_SUB = 1, IOP_MUL = 2 };
+
+template <int w, int OP, class W> BSFP_HD void int_op(const W* a, const W* b, W* r) {
+    if constexpr (OP == IOP_ADD) int_addsub<w, false>(a, b, r);
+    else if constexpr (OP == IOP_SUB) int_addsub<w, true>(a, b, r);
+    else int_mul<w>(a, b, r);
+}
+
 /* --------------------------------------------------------- conversions --- */
 /* r (1/E/M, B slices) = x (IEEE binary32, 32 slices: slice 0 the fraction's
  * least significant bit, slice 31 the sign), rounded once in mode RZ/FTZ --

@@ -74,3 +74,30 @@ extern "C" long BSFP_GC_CAT(bsfp_gate_count_e, BSFP_E)(int man_bits, int rnd, in
     if (man_bits < 1 || man_bits > 23 || op < 0 || op > 4 || rnd < 0 || rnd > 3) return -1;
     return bsfp::gc::count_m<BSFP_E, 1>(man_bits, rnd, op);
 }
+
+#if BSFP_E == 2
+/* Gates per word of the w-bit integer ops (compiled once, with the E = 2 unit). */
+namespace bsfp {
+namespace gc {
+namespace {
+template <int w> static long count_int(int bits, int op) {
+    if (bits == w) {
+        Graph g;
+        GW r[w];
+        if (op == 0) record_int<w, IOP_ADD>(g, r);
+        else if (op == 1) record_int<w, IOP_SUB>(g, r);
+        else record_int<w, IOP_MUL>(g, r);
+        return count_live(g, r, w);
+    }
+    if constexpr (w < 32) return count_int<w + 1>(bits, op);
+    return -1;
+}
+}  // namespace
+}  // namespace gc
+}  // namespace bsfp
+
+extern "C" long bsfp_int_gate_count_impl(int bits, int op) {
+    if (bits < 1 || bits > 32 || op < 0 || op > 2) return -1;
+    return bsfp::gc::count_int<1>(bits, op);
+}
+#endif

@@ -214,6 +214,19 @@ template <int E, int M, int R, int OP> static void record(Graph& g, GW* r) {
     g_graph = nullptr;
 }
 
+/* Record int_op<w, OP> over inputs a = ids 1..w, b = w+1..2w. */
+template <int w, int OP> static void record_int(Graph& g, GW* r) {
+    g.ninputs = 2 * w;
+    g_graph = &g;
+    GW a[w], b[w];
+    for (int i = 0; i < w; ++i) {
+        a[i] = GW((1 + i) << 1, 0);
+        b[i] = GW((1 + w + i) << 1, 0);
+    }
+    int_op<w, OP>(a, b, r);
+    g_graph = nullptr;
+}
+
 }  // namespace
 }  // namespace gc
 }  // namespace bsfp

@@ -99,3 +99,35 @@ extern "C" int host_convert(int e, int m, int rnd, int dir, const uint32_t* a, u
     FMTC(8, 23) FMTC(6, 9) FMTC(7, 13) FMTC(3, 23) FMTC(2, 23) FMTC(8, 1)
     return -1;
 }
+
+template <int w>
+static int run_int(int op, const uint32_t* a, const uint32_t* b, uint32_t* out, long nwords, long S) {
+    if constexpr (w > 32) {
+        return -1;
+    } else {
+        for (long k = 0; k < nwords; ++k) {
+            uint32_t x[w], y[w], r[w];
+            for (int i = 0; i < w; ++i) {
+                x[i] = a[i * S + k];
+                y[i] = b[i * S + k];
+            }
+            if (op == 0) int_op<w, IOP_ADD>(x, y, r);
+            else if (op == 1) int_op<w, IOP_SUB>(x, y, r);
+            else int_op<w, IOP_MUL>(x, y, r);
+            for (int i = 0; i < w; ++i) out[i * S + k] = r[i];
+        }
+        return 0;
+    }
+}
+
+template <int w>
+static int dispatch_int(int bits, int op, const uint32_t* a, const uint32_t* b, uint32_t* out, long nwords, long S) {
+    if (bits == w) return run_int<w>(op, a, b, out, nwords, S);
+    if constexpr (w < 32) return dispatch_int<w + 1>(bits, op, a, b, out, nwords, S);
+    return -1;
+}
+
+/* w-bit integer vectors: op 0 add, 1 sub, 2 mul */
+extern "C" int host_int(int bits, int op, const uint32_t* a, const uint32_t* b, uint32_t* out, long nwords, long S) {
+    return dispatch_int<1>(bits, op, a, b, out, nwords, S);
+}

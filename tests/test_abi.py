@@ -184,3 +184,19 @@ def test_conversion_arguments_validated_before_any_cuda_call():
     assert L.bsfp_from_float(f, 0, 256, 0, 256, None) == bs.OK
     assert L.bsfp_to_float(f, 256, 10, 258, None) == bs.ERR_ALIGN
     assert L.bsfp_to_float(bs.Format(6, 9, bs.RZ_FTZ), 256, 10, 256, None) == bs.ERR_UNSUPPORTED
+
+
+def test_integer_vectors_validated_before_any_cuda_call():
+    L = _binding._lib()
+    for fn in (L.bsfp_int_add, L.bsfp_int_sub, L.bsfp_int_mul):
+        assert fn(0, 256, 256, 256, 10, None) == bs.ERR_FORMAT
+        assert fn(33, 256, 256, 256, 10, None) == bs.ERR_FORMAT
+        assert fn(5, 256, 256, 256, -1, None) == bs.ERR_SIZE
+        assert fn(5, None, 256, 256, 10, None) == bs.ERR_NULL
+        assert fn(5, 264, 256, 256, 10, None) == bs.ERR_ALIGN
+        assert fn(5, 256, 256, 256, 0, None) == bs.OK
+    assert L.bsfp_int_pack(9, 257, 10, 256, None) == bs.ERR_ALIGN
+    assert L.bsfp_int_unpack(40, 256, 10, 256, None) == bs.ERR_FORMAT
+    # gates per word: the Fig. 2 adder is two 3-input gates per slice but the first
+    assert [bs.bsfp_int_gate_count(w, "add") for w in (1, 5, 13)] == [1, 9, 25]
+    assert bs.bsfp_int_gate_count(33, "add") == -1

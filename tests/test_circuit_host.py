@@ -34,6 +34,8 @@ def _lib():
         L.host_circuit.restype = ctypes.c_int
         L.host_convert.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 2 + [ctypes.c_long] * 2
         L.host_convert.restype = ctypes.c_int
+        L.host_int.argtypes = [ctypes.c_int] * 2 + [ctypes.c_void_p] * 3 + [ctypes.c_long] * 2
+        L.host_int.restype = ctypes.c_int
         _L = L
     return _L
 
@@ -201,3 +203,22 @@ def test_conversion_circuits(E, M, rnd):
     got = convert(E, M, rnd, 1, y)
     want = oracle.to_f32(E, M, rnd, y)
     assert (got == want).all(), "to: " + _first_bad(got, want, y)
+
+
+@pytest.mark.parametrize("w", [1, 2, 3, 5, 8, 9, 13, 16, 17, 24, 31, 32])
+def test_integer_circuits(w):
+    """The Sec. 3 integer circuits (ripple adder, truncated array multiplier)
+    against the oracle: every operand pair for w <= 7, samples beyond."""
+    if w <= 7:
+        a, b = synth.all_pairs(w)
+        a, b = a.astype(np.uint32), b.astype(np.uint32)
+    else:
+        a, b = (synth.uniform_bits(w, 1 << 15, 700 + w, k).astype(np.uint32) for k in range(2))
+    pa, pb = oracle.pack(w, a), oracle.pack(w, b)
+    S = pa.shape[1]
+    for op, code in (("add", 0), ("sub", 1), ("mul", 2)):
+        out = np.zeros_like(pa)
+        assert _lib().host_int(w, code, pa.ctypes.data, pb.ctypes.data, out.ctypes.data, S, S) == 0
+        got = oracle.unpack(w, out, a.size)
+        want = oracle.int_binop(op, w, a, b)
+        assert (got == want).all(), "%s w=%d: %s" % (op, w, _first_bad(got, want, a, b))
