@@ -750,7 +750,7 @@ def main(argv=None):
     ap.add_argument("--e2e-depth", type=int, default=0, help="pipeline streams (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-sample", type=int, default=1 << 20,
+    ap.add_argument("--ref-sample", type=int, default=1 << 23,
                     help="reference arm: elements per vector per step")
     ap.add_argument("--batch-jobs", type=int, default=4096,
                     help="vectors in the batched comparison (0 skips it)")
