@@ -366,6 +366,21 @@ bsfp_status bsfp_server_get_stats(bsfp_server srv, bsfp_server_stats* st);
  * requests are dropped, results become invalid. */
 void bsfp_server_destroy(bsfp_server srv);
 
+/* ----------------------------------------------------------- autotuning --- */
+/* Time every compiled launch shape of (f, op) -- words per thread x resident
+ * blocks per SM -- on scratch operands of 2^28 elements that this call
+ * allocates and frees (zeros; the circuits' timing does not depend on the
+ * values), keep the fastest for this process, and, if cache_path is not
+ * NULL, record it in that text cache (one line per format, rounding and op;
+ * an earlier line for the same key is replaced).  Synchronous; uses a stream
+ * of its own.  The north-star's autotuner; not part of the paper.  Errors:
+ * bad format or op as the ops; CUDA failures BSFP_ERR_CUDA; an unwritable
+ * cache BSFP_ERR_NULL (the shape is still applied). */
+bsfp_status bsfp_autotune(bsfp_format f, int32_t op, const char* cache_path);
+/* Apply every shape recorded in a cache written by bsfp_autotune; returns how
+ * many were applied, or -1 if the file cannot be read. */
+int32_t bsfp_autotune_load(const char* cache_path);
+
 /* ---------------------------------------------------------- diagnostics --- */
 const char* bsfp_status_str(int32_t status);
 /* The cudaError_t of the last BSFP_ERR_CUDA on this thread (0 if none). */

@@ -118,6 +118,8 @@ def _lib():
                 "bsfp_int_sub": (i32, [i32, p, p, p, i64, p]),
                 "bsfp_int_mul": (i32, [i32, p, p, p, i64, p]),
                 "bsfp_int_gate_count": (i64, [i32, i32]),
+                "bsfp_autotune": (i32, [F, i32, ctypes.c_char_p]),
+                "bsfp_autotune_load": (i32, [ctypes.c_char_p]),
                 "bsfp_to_float": (i32, [F, p, i64, p, p]),
                 "bsfp_status_str": (ctypes.c_char_p, [i32]),
                 "bsfp_last_cuda_error": (i32, []),
@@ -316,6 +318,17 @@ def bsfp_variants_compiled(f, op) -> list:
 
 def bsfp_set_variant(f, op, wpt: int, blocks_per_sm: int = 0):
     _check(_lib().bsfp_set_variant(_fmt(f), OPS.get(op, op), wpt, blocks_per_sm), "bsfp_set_variant")
+
+
+def bsfp_autotune(f, op, cache_path: str | None = None):
+    """Native autotuner: time every compiled shape of (f, op) at 2^28 elements,
+    apply the fastest, optionally record it in a text cache."""
+    _check(_lib().bsfp_autotune(_fmt(f), OPS.get(op, op), cache_path.encode() if cache_path else None),
+           "bsfp_autotune")
+
+
+def bsfp_autotune_load(cache_path: str) -> int:
+    return int(_lib().bsfp_autotune_load(cache_path.encode()))
 
 
 def bsfp_launch_count() -> int:

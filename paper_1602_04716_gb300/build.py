@@ -56,7 +56,7 @@ def _units():
                                                os.path.join(CSRC, "int_ops.cu")]))
     for opc in range(3):
         units.append(("batch_opc%d.o" % opc, cu + ["-DBSFP_BATCH_OPC=%d" % opc, os.path.join(CSRC, "batch_inst.cu")]))
-    for src in ("api.cu", "batch.cu", "batch_noalloc.cu", "serve.cu", "pipeline.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):
+    for src in ("api.cu", "batch.cu", "batch_noalloc.cu", "serve.cu", "pipeline.cu", "autotune.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):
         units.append((src.replace(".cu", ".o"), cu + [os.path.join(CSRC, src)]))
     return units
 

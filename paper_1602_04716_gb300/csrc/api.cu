@@ -69,8 +69,13 @@ static std::mutex g_shape_mu;
 static std::atomic<int64_t> g_launches{0};
 static thread_local int32_t g_last_cuda = 0;
 
+/* Record a CUDA failure for bsfp_last_cuda_error and clear the runtime's
+ * per-thread last-error slot: a refused cudaMalloc, say, must not surface
+ * later as the "launch error" of an unrelated kernel (ours or the caller's)
+ * checked with cudaGetLastError. */
 static bsfp_status cuda_fail(cudaError_t e) {
     g_last_cuda = (int32_t)e;
+    (void)cudaGetLastError();
     return BSFP_ERR_CUDA;
 }
 
@@ -166,6 +171,16 @@ bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s) {
 }
 
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+bsfp_status run_op_by_code(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                           uint32_t* out, int64_t n, cudaStream_t s) {
+    PreparedOp po;
+    const bsfp_status st = prepare_binop(f, op, a, b, c, out, n, &po);
+    if (st != BSFP_OK || po.skip) return st;
+    const bsfp_status r = launch_prepared(po, s);
+    if (r == BSFP_OK) count_launches(1);
+    return r;
+}
 
 bsfp_status set_cuda_error(cudaError_t e) { return cuda_fail(e); }
 

@@ -64,6 +64,7 @@ extern "C" {
 
 bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bsfp_batch_options* opt,
                                    bsfp_batch_plan* plan_out) {
+    NvtxRange range("bsfp_batch_plan_create");
     if (!plan_out) return BSFP_ERR_NULL;
     *plan_out = nullptr;
     if (njobs < 0) return BSFP_ERR_SIZE;
@@ -209,6 +210,7 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
 }
 
 bsfp_status bsfp_batch_run(bsfp_batch_plan plan, bsfp_stream_t s) {
+    NvtxRange range("bsfp_batch_run");
     if (!plan) return BSFP_ERR_NULL;
     const cudaError_t err = cudaGraphLaunch(plan->exec, (cudaStream_t)s);
     if (err != cudaSuccess) return set_cuda_error(err);

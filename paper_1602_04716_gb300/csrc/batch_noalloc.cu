@@ -224,6 +224,7 @@ bsfp_status noalloc_setup(int dev, NoallocDevice** out) {
 using namespace bsfp;
 
 extern "C" bsfp_status bsfp_batch_run_noalloc(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s) {
+    NvtxRange range("bsfp_batch_run_noalloc");
     if (njobs < 0 || njobs > BSFP_NOALLOC_MAX_JOBS) return BSFP_ERR_SIZE;
     if (njobs == 0) return BSFP_OK;
     if (!jobs) return BSFP_ERR_NULL;

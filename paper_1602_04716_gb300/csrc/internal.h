@@ -6,10 +6,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "binop.cuh"
 #include "bsfp.h"
 
 namespace bsfp {
+
+/* An NVTX range for the library's coarse phases (batch plans and runs,
+ * server micro-batches, pipeline runs, autotuning); free without a tool. */
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 /* A validated element-wise op, ready to launch. */
 struct PreparedOp {
@@ -30,5 +41,8 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
 bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s);
 void count_launches(int64_t k);
 bsfp_status set_cuda_error(cudaError_t e);
+/* Launch op (bsfp_op code) on stream s through the public entry points. */
+bsfp_status run_op_by_code(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                           uint32_t* out, int64_t n, cudaStream_t s);
 
 }  // namespace bsfp

@@ -143,6 +143,7 @@ bsfp_status bsfp_pipeline_create(int64_t chunk, int32_t depth, bsfp_pipeline* ou
 
 bsfp_status bsfp_pipeline_run(bsfp_pipeline P, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,
                               const void* b, const void* c, void* const* outs, int64_t n) {
+    NvtxRange range("bsfp_pipeline_run");
     if (!P || !ops || !outs) return BSFP_ERR_NULL;
     if (!format_ok(f)) return BSFP_ERR_FORMAT;
     if (nops < 1 || nops > BSFP_PIPE_MAX_OPS || n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;

@@ -187,6 +187,7 @@ void bsfp_server_st::retire_locked(Slot& s, bool ok, cudaError_t err) {
 /* Admit from the head of the FIFO into slot s and launch; false if nothing
  * could be admitted. */
 bool bsfp_server_st::admit_locked(Slot& s) {
+    NvtxRange range("bsfp_server micro-batch");
     int32_t njob_c[OPC_COUNT] = {0, 0, 0};
     int64_t ntile_c[OPC_COUNT] = {0, 0, 0};
     int64_t tiles = 0;

@@ -200,3 +200,19 @@ def test_integer_vectors_validated_before_any_cuda_call():
     # gates per word: the Fig. 2 adder is two 3-input gates per slice but the first
     assert [bs.bsfp_int_gate_count(w, "add") for w in (1, 5, 13)] == [1, 9, 25]
     assert bs.bsfp_int_gate_count(33, "add") == -1
+
+
+def test_autotune_arguments_and_cache_loading(tmp_path):
+    L = _binding._lib()
+    assert L.bsfp_autotune(bs.Format(9, 7), 0, None) == bs.ERR_FORMAT
+    assert L.bsfp_autotune(bs.Format(5, 7), 9, None) == bs.ERR_UNSUPPORTED
+    assert L.bsfp_autotune(bs.Format(6, 9, bs.RN_FTZ), 2, None) == bs.ERR_UNSUPPORTED
+    assert bs.bsfp_autotune_load(str(tmp_path / "missing")) == -1
+    cache = tmp_path / "shapes.txt"
+    # E M rounding op wpt blocks/SM ms: two valid shapes, one not compiled (wpt 4 for 1/6/9), a comment
+    cache.write_text("# test\n5 7 0 2 2 3 0.1\n4 4 1 0 1 0 0.2\n6 9 0 2 4 0 0.3\n")
+    assert bs.bsfp_autotune_load(str(cache)) == 2
+    assert bs.bsfp_variant(bs.Format(5, 7, 0), "mul") == 2
+    assert bs.bsfp_variant(bs.Format(4, 4, 1), "add") == 1
+    bs.bsfp_set_variant(bs.Format(5, 7, 0), "mul", 0, 0)
+    bs.bsfp_set_variant(bs.Format(4, 4, 1), "add", 0, 0)

@@ -346,3 +346,69 @@ def test_full_size_2_28_sampled(E, M):
         assert not len(bad), "%s: %d bad, first idx %d" % (op, len(bad), idx[bad[0]])
     del planes, out, std
     torch.cuda.empty_cache()
+
+
+def test_native_autotune_applies_and_records_a_shape(tmp_path):
+    f = bs.Format(5, 7, oracle.RN)
+    cache = tmp_path / "shapes.txt"
+    bs.bsfp_autotune(f, "mul", str(cache))
+    lines = [l.split() for l in cache.read_text().splitlines() if not l.startswith("#")]
+    assert len(lines) == 1 and lines[0][:4] == ["5", "7", "0", "2"]
+    assert bs.bsfp_variant(f, "mul") == int(lines[0][4])
+    n = 70_001
+    a, b = (synth.fp_values(5, 7, n, s).astype(np.uint32) for s in (81, 82))
+    check("mul", 5, 7, oracle.RN, a, b)          # results do not depend on the shape
+    bs.bsfp_autotune(f, "add", str(cache))       # a second entry is appended, the first kept
+    lines = [l.split() for l in cache.read_text().splitlines() if not l.startswith("#")]
+    assert sorted(l[3] for l in lines) == ["0", "2"]
+    bs.bsfp_set_variant(f, "mul", 0, 0)
+    bs.bsfp_set_variant(f, "add", 0, 0)
+
+
+# ------------------------------------------------------- guard words ---
+def test_no_kernel_writes_outside_its_output():
+    """Every kernel family writes into a buffer framed by 4 KiB of guard words
+    on each side (compute-sanitizer is closed on this machine): the guards must
+    come back untouched and the payload must match the oracle."""
+    G = 1024   # guard words on each side
+    pat = np.int32(0x5A5A5A5A)
+
+    def framed(words):
+        t = torch.full((words + 2 * G,), int(pat), dtype=torch.int32, device="cuda")
+        return t, t[G:G + words]
+
+    def guards_ok(t, words):
+        h = t.cpu().numpy()
+        return (h[:G] == pat).all() and (h[G + words:] == pat).all()
+
+    for E, M, n in ((5, 7, 1000), (4, 3, 33), (8, 23, 4097), (6, 9, 70001)):
+        B = 1 + E + M
+        S = bs.bsfp_plane_stride(n)
+        a, b = (synth.fp_values(E, M, n, s).astype(np.uint32) for s in (91, 92))
+        pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+        for op in ("add", "mul", "div"):
+            t, out = framed(B * S)
+            bs.bsfp_op(op, bs.Format(E, M), pa, pb, out, n)
+            torch.cuda.synchronize()
+            assert guards_ok(t, B * S), "%s 1/%d/%d wrote outside" % (op, E, M)
+        std_words = (n * bs.bsfp_container_bytes(bs.Format(E, M)) + 3) // 4
+        t, out = framed(std_words)
+        bs.bsfp_unpack(bs.Format(E, M), pa, n, out)
+        torch.cuda.synchronize()
+        assert guards_ok(t, std_words), "unpack 1/%d/%d wrote outside" % (E, M)
+        t, out = framed(n)
+        bs.bsfp_to_float(bs.Format(E, M), pa, n, out)
+        torch.cuda.synchronize()
+        assert guards_ok(t, n), "to_float 1/%d/%d wrote outside" % (E, M)
+        src = torch.zeros(n, dtype=torch.float32, device="cuda")
+        t, out = framed(B * S)
+        bs.bsfp_from_float(bs.Format(E, M), src, n, out)
+        torch.cuda.synchronize()
+        assert guards_ok(t, B * S), "from_float 1/%d/%d wrote outside" % (E, M)
+    for w, n in ((5, 100), (13, 4097), (32, 33)):
+        S = bs.bsfp_plane_stride(n)
+        x = torch.zeros(w * S, dtype=torch.int32, device="cuda")
+        t, out = framed(w * S)
+        bs.bsfp_int_op("mul", w, x, x, out, n)
+        torch.cuda.synchronize()
+        assert guards_ok(t, w * S), "int mul w=%d wrote outside" % w

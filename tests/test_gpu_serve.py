@@ -149,3 +149,17 @@ def test_budget_errors_and_bounded_drain():
         one.release(r2)           # released twice
     assert one.stats()["arena_peak_bytes"] <= (need + 255) // 256 * 256
     one.close()
+
+
+def test_allocation_failure_is_reported_and_leaves_nothing_behind():
+    """A budget far beyond the device's memory: creation fails with
+    BSFP_ERR_CUDA (a refused cudaMalloc, not a fault), and the device stays
+    usable with its free memory unchanged."""
+    free0, _ = torch.cuda.mem_get_info()
+    with pytest.raises(bs.BsfpError) as ei:
+        bs.Server(1 << 50)
+    assert ei.value.status == bs.ERR_CUDA
+    free1, _ = torch.cuda.mem_get_info()
+    assert abs(free1 - free0) < (64 << 20)
+    srv = bs.Server(1 << 20)      # still works afterwards
+    srv.close()
