@@ -390,20 +390,41 @@ int32_t bsfp_last_cuda_error(void);
  * gates dropped): the work term of the logic roofline.  Table 1 of Sec. 4
  * gives only the asymptotic classes.  -1 on a bad argument. */
 int64_t bsfp_gate_count(bsfp_format f, int32_t op);
-/* Words per thread the op kernel will use for (format, op): 1, 2 or 4; -1 on
- * a bad argument, 0 if the format is not compiled. */
+/* Kernel variants of an element-wise op.  1, 2 and 4 are the grid-stride
+ * kernel with that many words per thread.  BSFP_VARIANT_STREAMED is the
+ * streamed kernel: one block per SM; a producer warp brings the operands'
+ * planes into a shared-memory ring with TMA bulk copies (cp.async.bulk,
+ * completed on mbarriers) while consumer warps run the circuit from it.  It
+ * is compiled for add/sub and mul of 1/4/3, 1/4/4, 1/5/7, 1/5/10 and 1/8/7
+ * in every rounding mode.  Results are identical in every variant; only the
+ * speed differs.  (Not a construct of the paper, whose kernels are CPU
+ * loops; Sec. 4 leaves the memory schedule to the implementation.) */
+#define BSFP_VARIANT_STREAMED 8
+/* Variant the op kernel will use for (format, op): 1, 2, 4 or
+ * BSFP_VARIANT_STREAMED; -1 on a bad argument, 0 if the format is not
+ * compiled. */
 int32_t bsfp_variant(bsfp_format f, int32_t op);
-/* Bit mask of the words-per-thread variants compiled for (format, op):
- * bit 0 = 1, bit 1 = 2, bit 2 = 4. */
+/* Bit mask of the variants compiled for (format, op): bit 0 = 1, bit 1 = 2,
+ * bit 2 = 4, bit 3 = BSFP_VARIANT_STREAMED. */
 int32_t bsfp_variants_compiled(bsfp_format f, int32_t op);
-/* Override the launch shape for (format, op): wpt in {1,2,4} (must be
- * compiled; 0 restores the default) and blocks_per_sm (0 = occupancy
- * maximum, larger values are capped at it).  sub shares add's shape.  Used by
- * the autotuner; returns BSFP_ERR_UNSUPPORTED for an uncompiled wpt.  Not
- * synchronised with launches already queued: it affects later calls. */
+/* Override the launch shape for (format, op): wpt in {1, 2, 4,
+ * BSFP_VARIANT_STREAMED} (must be compiled; 0 restores the default) and
+ * blocks_per_sm (0 = occupancy maximum, larger values are capped at it;
+ * ignored by the streamed kernel, which runs one block per SM).  sub shares
+ * add's shape.  Used by the autotuner; returns BSFP_ERR_UNSUPPORTED for an
+ * uncompiled variant.  Not synchronised with launches already queued: it
+ * affects later calls. */
 bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blocks_per_sm);
 /* Kernel launches this library has issued on this process so far. */
 int64_t bsfp_launch_count(void);
+/* Fault word of the current device: 0 if no kernel has reported a fault,
+ * 1 if a streamed kernel gave up a wait on its copy pipeline (each wait is
+ * bounded at 2^32 SM clock cycles, about two seconds; the kernel then stops,
+ * lets its copies in flight land and returns, leaving its output
+ * incomplete).  Synchronises the device first; clear != 0 resets the word.
+ * -1 if the word cannot be read (see bsfp_last_cuda_error).  No counterpart
+ * in the paper. */
+int32_t bsfp_fault_status(int32_t clear);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,7 @@ OPS = {"add": OP_ADD, "sub": OP_SUB, "mul": OP_MUL, "fma2": OP_FMA2, "div": OP_D
 
 OK = 0
 ERR_FORMAT, ERR_NULL, ERR_ALIGN, ERR_SIZE, ERR_UNSUPPORTED, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT = range(-1, -9, -1)
+VARIANT_STREAMED = 8
 PROBE_LOP3_PER_ROUND = 64
 MAX_N = 1 << 40
 
@@ -128,6 +129,7 @@ def _lib():
                 "bsfp_variants_compiled": (i32, [F, i32]),
                 "bsfp_set_variant": (i32, [F, i32, i32, i32]),
                 "bsfp_launch_count": (i64, []),
+                "bsfp_fault_status": (i32, [i32]),
                 "bsfp_synth_fp_values": (i32, [F, i64, u64, u64, i64, p, p]),
                 "bsfp_lop3_probe": (i32, [p, i32, i32, i32, u32, p]),
                 "bsfp_num_sms": (i32, []),
@@ -312,8 +314,19 @@ def bsfp_variant(f, op) -> int:
 
 
 def bsfp_variants_compiled(f, op) -> list:
+    """Variants compiled for (f, op): words per thread 1, 2, 4 of the
+    grid-stride kernel and VARIANT_STREAMED (8) for the streamed kernel."""
     m = int(_lib().bsfp_variants_compiled(_fmt(f), OPS.get(op, op)))
-    return [w for i, w in enumerate((1, 2, 4)) if m > 0 and (m >> i) & 1]
+    return [w for i, w in enumerate((1, 2, 4, VARIANT_STREAMED)) if m > 0 and (m >> i) & 1]
+
+
+def bsfp_fault_status(clear: bool = False) -> int:
+    """The current device's fault word (0: none; 1: a streamed kernel gave up
+    a bounded wait).  Synchronises the device."""
+    v = int(_lib().bsfp_fault_status(1 if clear else 0))
+    if v < 0:
+        raise BsfpError(ERR_CUDA, "bsfp_fault_status")
+    return v
 
 
 def bsfp_set_variant(f, op, wpt: int, blocks_per_sm: int = 0):

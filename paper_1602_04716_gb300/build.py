@@ -27,6 +27,9 @@ GEN_HEADER = os.path.join(GEN_DIR, "gen_circuits.cuh")
 # Formats whose circuits are printed gate by gate from their netlists
 # (circuitgen): the formats of the benchmarks and of the batched kernels.
 GEN_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]
+# Formats with a streamed kernel (stream.cuh): the generated formats of at
+# most 16 planes.
+STREAM_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
 
 
 def nvcc() -> str:
@@ -54,6 +57,9 @@ def _units():
     for lo, hi in ((1, 16), (17, 32)):
         units.append(("int_w%d.o" % lo, cu + ["-DBSFP_W_LO=%d" % lo, "-DBSFP_W_HI=%d" % hi,
                                                os.path.join(CSRC, "int_ops.cu")]))
+    for e, m in STREAM_FORMATS:
+        units.append(("stream_e%d_m%d.o" % (e, m), cu + ["-DBSFP_SE=%d" % e, "-DBSFP_SM=%d" % m,
+                                                         os.path.join(CSRC, "stream_inst.cu")]))
     for opc in range(3):
         units.append(("batch_opc%d.o" % opc, cu + ["-DBSFP_BATCH_OPC=%d" % opc, os.path.join(CSRC, "batch_inst.cu")]))
     for src in ("api.cu", "batch.cu", "batch_noalloc.cu", "serve.cu", "pipeline.cu", "autotune.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):

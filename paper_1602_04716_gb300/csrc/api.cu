@@ -38,6 +38,9 @@ BSFP_DECL_REG(8)
 void register_conv_e2(); void register_conv_e3(); void register_conv_e4(); void register_conv_e5();
 void register_conv_e6(); void register_conv_e7(); void register_conv_e8();
 void register_int_w1(); void register_int_w17();
+/* streamed kernels, one translation unit per format (stream_inst.cu) */
+void register_stream_e4_m3(); void register_stream_e4_m4(); void register_stream_e5_m7();
+void register_stream_e5_m10(); void register_stream_e8_m7();
 
 cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st);
 cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st);
@@ -54,6 +57,42 @@ static void init_tables() {
     register_conv_e2(); register_conv_e3(); register_conv_e4(); register_conv_e5();
     register_conv_e6(); register_conv_e7(); register_conv_e8();
     register_int_w1(); register_int_w17();
+    /* after the grid-stride kernels: these extend their entries */
+    register_stream_e4_m3(); register_stream_e4_m4(); register_stream_e5_m7();
+    register_stream_e5_m10(); register_stream_e8_m7();
+}
+
+/* Devices on which a streamed kernel has opted in to its shared memory, one
+ * bit per device, per (E, M, rounding, op class). */
+static std::atomic<uint64_t> g_stream_ready[TAB_E][TAB_M][TAB_R][OPC_ALL];
+
+/* The fault word the streamed kernels set when a wait runs out of time, per
+ * device (its address is looked up once per device). */
+static __device__ int g_fault_word;
+static std::atomic<int*> g_fault_addr[64];
+
+static int current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1;
+    }
+    return dev;
+}
+
+static int* fault_word(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    int* p = g_fault_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_fault_word) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        p = static_cast<int*>(a);
+        g_fault_addr[dev].store(p, std::memory_order_release);
+    }
+    return p;
 }
 
 /* Launch shape per (E, M, rounding, op class): words per thread and resident
@@ -147,13 +186,35 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
     po->entry = e;
     po->opc = opc;
 
+    const int dev = current_device();
+    p.fault = fault_word(dev);
     int wpt, bps;
     {
         std::lock_guard<std::mutex> lk(g_shape_mu);
         const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
         wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
-        const int occ = occupancy(f, opc, e, wpt);
-        bps = (sh.bps > 0 && sh.bps < occ) ? sh.bps : occ;
+        if (wpt == VARIANT_STREAMED) {
+            bps = 1;
+        } else {
+            const int occ = occupancy(f, opc, e, wpt);
+            bps = (sh.bps > 0 && sh.bps < occ) ? sh.bps : occ;
+        }
+    }
+    if (wpt == VARIANT_STREAMED) {
+        /* one block per SM (the ring takes its shared memory), one tile of
+         * stream_tw word columns per block at a time */
+        std::atomic<uint64_t>& ready = g_stream_ready[f.exp_bits][f.man_bits][f.rnd][opc];
+        const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+        if (!bit || !(ready.load(std::memory_order_acquire) & bit)) {
+            const cudaError_t err = e->stream_prepare();
+            if (err != cudaSuccess) return cuda_fail(err);
+            ready.fetch_or(bit, std::memory_order_acq_rel);
+        }
+        const int64_t tiles = (p.S + e->stream_tw - 1) / e->stream_tw;
+        const int64_t sms = device_num_sms();
+        po->wpt = wpt;
+        po->grid = (int)(tiles < sms ? tiles : sms);
+        return BSFP_OK;
     }
     const int64_t chunks = p.S / wpt;
     const int64_t need = (chunks + 127) / 128;
@@ -165,7 +226,8 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
 
 bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s) {
     if (po.skip) return BSFP_OK;
-    const cudaError_t err = po.entry->launch(po.args, po.wpt, po.grid, s);
+    const cudaError_t err = (po.wpt == VARIANT_STREAMED) ? po.entry->stream_launch(po.args, po.grid, s)
+                                                         : po.entry->launch(po.args, po.wpt, po.grid, s);
     if (err != cudaSuccess) return cuda_fail(err);
     return BSFP_OK;
 }
@@ -437,7 +499,7 @@ bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blo
     if (!format_ok(f)) return BSFP_ERR_FORMAT;
     const int opc = opclass(op);
     if (opc < 0 || blocks_per_sm < 0 || blocks_per_sm > 64) return BSFP_ERR_SIZE;
-    if (wpt != 0 && wpt != 1 && wpt != 2 && wpt != 4) return BSFP_ERR_SIZE;
+    if (wpt != 0 && wpt != 1 && wpt != 2 && wpt != 4 && wpt != VARIANT_STREAMED) return BSFP_ERR_SIZE;
     const BinopEntry* e = entry_for(f, opc);
     if (!e || (wpt != 0 && !(e->wpt_mask & (unsigned)wpt))) return BSFP_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_shape_mu);
@@ -446,5 +508,22 @@ bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blo
 }
 
 int64_t bsfp_launch_count(void) { return g_launches.load(); }
+
+int32_t bsfp_fault_status(int32_t clear) {
+    int* p = fault_word(current_device());
+    if (!p) return -1;
+    int v = 0;
+    cudaError_t err = cudaDeviceSynchronize();
+    if (err == cudaSuccess) err = cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost);
+    if (err == cudaSuccess && clear && v) {
+        const int zero = 0;
+        err = cudaMemcpy(p, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    }
+    if (err != cudaSuccess) {
+        cuda_fail(err);
+        return -1;
+    }
+    return v;
+}
 
 }  // extern "C"

@@ -68,9 +68,11 @@ bsfp_status bsfp_autotune(bsfp_format f, int32_t op, const char* cache_path) {
     int best_wpt = 0, best_bps = 0;
     float best = 1e30f;
     bsfp_status st = e == cudaSuccess ? BSFP_OK : set_cuda_error(e);
-    for (int wpt = 1; wpt <= 4 && st == BSFP_OK; wpt <<= 1) {
+    for (int wpt = 1; wpt <= BSFP_VARIANT_STREAMED && st == BSFP_OK; wpt <<= 1) {
         if (!(mask & wpt)) continue;
         for (int bps : bps_choices) {
+            /* the streamed kernel runs one block per SM: one shape only */
+            if (wpt == BSFP_VARIANT_STREAMED && bps != 0) continue;
             st = bsfp_set_variant(f, op, wpt, bps);
             std::vector<float> t;
             for (int r = 0; r < 6 && st == BSFP_OK; ++r) {

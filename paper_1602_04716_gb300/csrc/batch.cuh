@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const JobDesc* __restrict__ 
         p.nwords = d.nwords;
         p.tailmask = d.tailmask;
         p.negb = d.negb;
+        p.fault = nullptr;
         const int kind = d.kind;
         const int64_t base = (t - d.tile0) * TILE + (int64_t)threadIdx.x * WPT;
 #pragma unroll 1

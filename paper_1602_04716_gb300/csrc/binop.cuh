@@ -42,6 +42,8 @@ struct BinopArgs {
     int64_t nwords;      /* ceil(n / 32): columns that hold elements */
     uint32_t tailmask;   /* valid lanes of column nwords-1 */
     uint32_t negb;       /* ~0 flips b's sign slice (sub), 0 otherwise */
+    int* fault;          /* device word set to 1 if a streamed kernel's wait
+                            ran out of time; unused by the other kernels */
 };
 
 template <int WPT> struct VecT;
@@ -97,19 +99,12 @@ __device__ __forceinline__ void column_op(uint32_t* x, uint32_t* y, const uint32
     }
 }
 
-/* WPT word columns starting at w0 (a multiple of WPT). */
+/* The circuit on WPT word columns starting at w0 (a multiple of WPT) whose
+ * input slices are already in registers, then the masked stores. */
 template <int E, int M, int R, int OPC, int WPT>
-__device__ __forceinline__ void binop_chunk(const BinopArgs& p, int64_t w0) {
+__device__ __forceinline__ void binop_compute_store(const BinopArgs& p, int64_t w0, const uint32_t (*xa)[WPT],
+                                                    const uint32_t (*xb)[WPT], const uint32_t (*xc)[WPT]) {
     constexpr int B = 1 + E + M;
-    uint32_t xa[B][WPT], xb[B][WPT], xc[(OPC == OPC_FMA2) ? B : 1][WPT];
-#pragma unroll
-    for (int i = 0; i < B; ++i) vload<WPT>(p.a + i * p.S + w0, xa[i]);
-#pragma unroll
-    for (int i = 0; i < B; ++i) vload<WPT>(p.b + i * p.S + w0, xb[i]);
-    if constexpr (OPC == OPC_FMA2) {
-#pragma unroll
-        for (int i = 0; i < B; ++i) vload<WPT>(p.c + i * p.S + w0, xc[i]);
-    }
     uint32_t r[B][WPT];
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
@@ -137,6 +132,22 @@ __device__ __forceinline__ void binop_chunk(const BinopArgs& p, int64_t w0) {
     }
 #pragma unroll
     for (int i = 0; i < B; ++i) vstore<WPT>(p.out + i * p.S + w0, r[i]);
+}
+
+/* WPT word columns starting at w0 (a multiple of WPT). */
+template <int E, int M, int R, int OPC, int WPT>
+__device__ __forceinline__ void binop_chunk(const BinopArgs& p, int64_t w0) {
+    constexpr int B = 1 + E + M;
+    uint32_t xa[B][WPT], xb[B][WPT], xc[(OPC == OPC_FMA2) ? B : 1][WPT];
+#pragma unroll
+    for (int i = 0; i < B; ++i) vload<WPT>(p.a + i * p.S + w0, xa[i]);
+#pragma unroll
+    for (int i = 0; i < B; ++i) vload<WPT>(p.b + i * p.S + w0, xb[i]);
+    if constexpr (OPC == OPC_FMA2) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) vload<WPT>(p.c + i * p.S + w0, xc[i]);
+    }
+    binop_compute_store<E, M, R, OPC, WPT>(p, w0, xa, xb, xc);
 }
 
 template <int E, int M, int R, int OPC, int WPT>
@@ -167,12 +178,23 @@ constexpr unsigned wpt_mask(int E, int M, int opc) {
  * variants. */
 typedef cudaError_t (*binop_launch_fn)(const BinopArgs& p, int wpt, int grid, cudaStream_t s);
 typedef const void* (*binop_kernel_fn)(int wpt);
+typedef cudaError_t (*stream_launch_fn)(const BinopArgs& p, int grid, cudaStream_t s);
+typedef cudaError_t (*stream_prepare_fn)();
+
+/* Variant code of the streamed kernel (stream.cuh) beside the words-per-
+ * thread codes 1, 2 and 4 of the grid-stride kernel. */
+constexpr int VARIANT_STREAMED = 8;
 
 struct BinopEntry {
     binop_launch_fn launch;
     binop_kernel_fn kernel;   /* the __global__ function, for occupancy queries */
-    unsigned wpt_mask;        /* compiled variants: bit 0 = 1, bit 1 = 2, bit 2 = 4 */
+    unsigned wpt_mask;        /* compiled variants: bit 0 = 1, bit 1 = 2, bit 2 = 4,
+                                 bit 3 = the streamed kernel */
     int default_wpt;
+    /* the streamed kernel, where compiled (filled by stream_inst.cu) */
+    stream_launch_fn stream_launch = nullptr;
+    stream_prepare_fn stream_prepare = nullptr;   /* opts in to its shared memory */
+    int stream_tw = 0;                            /* words per plane per tile */
 };
 
 template <int E, int M, int R, int OPC>

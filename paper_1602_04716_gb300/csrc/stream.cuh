@@ -1,0 +1,154 @@
+/*
+ * stream.cuh -- the streamed element-wise kernel: the same circuits as
+ * binop.cuh, with the operands' planes brought into a shared-memory ring by
+ * TMA bulk copies instead of per-thread global loads.
+ *
+ * Layout and semantics are those of binop.cuh (Sec. 2, Fig. 1; Sec. 4,
+ * Table 1); only the movement of the input slices differs.  The grid-stride
+ * kernel alternates, warp by warp, between waiting for its loads and
+ * running the logic, so with few resident warps (the mul circuits need
+ * 120-170 registers a thread) the logic pipe idles while loads are in
+ * flight.  Here one block per SM splits the roles:
+ *
+ *   producer warp (lane 0): for each tile of TW word columns, waits until
+ *     ring stage k % NST is free, then issues one cp.async.bulk per input
+ *     plane (2B copies of TW*4 bytes) completing on that stage's `full`
+ *     mbarrier (expect_tx = all bytes of the stage);
+ *   NC consumer warps: wait on `full`, copy their 2 words of every plane
+ *     from shared memory into registers, release the stage (one arrive per
+ *     warp on `empty`) and run the circuit, storing the results straight to
+ *     global memory with 64-bit streaming stores.
+ *
+ * The ring keeps NST tiles of loads in flight whatever the consumers are
+ * doing, and the consumers never wait on global memory.  Tiles go to blocks
+ * round-robin (tile t to block t mod gridDim).  Shapes (consumer warps x
+ * stages) are fixed per plane count B so that the registers of NC+1 warps
+ * and the ring fit one SM: 16 x 3 for B <= 9, 15 x 2 for B = 13, 12 x 2 for
+ * B = 16 (measured against neighbouring shapes on 2^28-element operands).
+ *
+ * Waits are bounded (tma.cuh); a block whose wait gives up stops, lets its
+ * copies in flight land, and sets *p.fault, which bsfp_fault_status reports.
+ */
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "binop.cuh"
+#include "tma.cuh"
+
+namespace bsfp {
+
+/* Formats and op classes compiled with a streamed kernel. */
+constexpr bool stream_format(int E, int M) { return tuned_format(E, M) && 1 + E + M <= 16; }
+constexpr bool stream_opc(int opc) { return opc == OPC_ADDSUB || opc == OPC_MUL; }
+
+template <int E, int M>
+struct StreamShape {
+    static constexpr int B = 1 + E + M;
+    static constexpr int WPT = 2;                                   /* words per consumer thread */
+    static constexpr int NC = B <= 9 ? 16 : (B <= 13 ? 15 : 12);    /* consumer warps */
+    static constexpr int NST = B <= 9 ? 3 : 2;                      /* ring stages */
+    static constexpr int NIN = 2 * B;                               /* input planes per tile */
+    static constexpr int TW = 32 * NC * WPT;                        /* words per plane per tile */
+    static constexpr int THREADS = 32 * (NC + 1);
+    static constexpr int HDR = 128;                                 /* barriers */
+    static constexpr size_t SMEM = HDR + (size_t)NST * NIN * TW * 4;
+    static_assert(2 * NST * 8 <= HDR, "barriers fit the header");
+    static_assert(SMEM <= 232448, "ring fits the shared memory one block may opt in to");
+    static_assert((size_t)NIN * TW * 4 < (1u << 20), "a stage's bytes fit the transaction count");
+};
+
+/* The bound is on threads only: the block size alone caps registers at
+ * 65536 / THREADS.  Adding a minimum of one block per SM changes ptxas's
+ * register target and schedule and made the adders about 9% slower. */
+template <int E, int M, int R, int OPC>
+__global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_kernel(const BinopArgs p) {
+    using SH = StreamShape<E, M>;
+    constexpr int B = SH::B, NC = SH::NC, NST = SH::NST, NIN = SH::NIN, TW = SH::TW, WPT = SH::WPT;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + NST;
+    uint32_t* ring = reinterpret_cast<uint32_t*>(smem + SH::HDR);
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (p.S + TW - 1) / TW;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(smem_addr(&full[s]), 1);
+            mbar_init(smem_addr(&empty[s]), NC);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    volatile int* ab = &abort_flag;
+
+    if (warp == NC) {
+        /* producer */
+        if (lane == 0) {
+            int64_t k = 0;   /* tiles issued by this block */
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+                const int s = (int)(k % NST);
+                if (k >= NST && !mbar_wait(smem_addr(&empty[s]), (uint32_t)((k / NST - 1) & 1), ab)) break;
+                const int64_t rem = p.S - t * TW;   /* > 0, a multiple of 32 */
+                const uint32_t bytes = (uint32_t)((rem < TW ? rem : TW) * 4);
+                const uint32_t bar = smem_addr(&full[s]);
+                mbar_arrive_expect_tx(bar, bytes * NIN);
+                const uint32_t dst = smem_addr(ring + (size_t)s * NIN * TW);
+#pragma unroll 1
+                for (int q = 0; q < NIN; ++q) {
+                    const uint32_t* src = (q < B) ? p.a + (int64_t)q * p.S : p.b + (int64_t)(q - B) * p.S;
+                    bulk_copy_g2s(dst + (uint32_t)(q * TW * 4), src + t * TW, bytes, bar);
+                }
+            }
+            /* the last phase issued on each stage has landed before the
+             * block exits (at once, unless a wait gave up) */
+            for (int64_t j = k > NST ? k - NST : 0; j < k; ++j)
+                mbar_drain(smem_addr(&full[j % NST]), (uint32_t)((j / NST) & 1));
+            if (*ab && p.fault) atomicExch(p.fault, 1);
+        }
+        return;
+    }
+
+    /* consumers: thread (warp, lane) owns word columns j0, j0+1 of a tile */
+    const int j0 = (warp * 32 + lane) * WPT;
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = (int)(k % NST);
+        const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)((k / NST) & 1), ab);
+        if (!__all_sync(0xFFFFFFFFu, ok)) break;   /* the warp leaves together */
+        const uint32_t* src = ring + (size_t)s * NIN * TW + j0;
+        uint32_t xa[B][WPT], xb[B][WPT], xc[1][WPT];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+#pragma unroll
+            for (int w = 0; w < WPT; ++w) {
+                xa[i][w] = src[i * TW + w];
+                xb[i][w] = src[(B + i) * TW + w];
+            }
+        }
+        /* every lane's slices are in registers: release the stage */
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
+        const int64_t w0 = t * TW + j0;
+        /* S is a multiple of 32, so a pair of columns is all in or all out */
+        if (w0 < p.S) binop_compute_store<E, M, R, OPC, WPT>(p, w0, xa, xb, xc);
+    }
+    if (lane == 0 && *ab && p.fault) atomicExch(p.fault, 1);
+}
+
+template <int E, int M, int R, int OPC>
+cudaError_t stream_launch(const BinopArgs& p, int grid, cudaStream_t s) {
+    using SH = StreamShape<E, M>;
+    stream_kernel<E, M, R, OPC><<<grid, SH::THREADS, SH::SMEM, s>>>(p);
+    return cudaGetLastError();
+}
+
+/* Opt the kernel in to its ring's shared memory on the current device. */
+template <int E, int M, int R, int OPC>
+cudaError_t stream_prepare() {
+    return cudaFuncSetAttribute(stream_kernel<E, M, R, OPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)StreamShape<E, M>::SMEM);
+}
+
+}  // namespace bsfp

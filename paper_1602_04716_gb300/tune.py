@@ -73,10 +73,11 @@ def time_op(op, f, a, b, c, out, n, reps=5) -> float:
 
 def autotune(op, f, a, b, c, out, n, bps_choices=(0, 1, 2, 3, 4, 6, 8), reps=5, path: str | None = CACHE):
     """Time every (wpt, blocks/SM) shape; set and (optionally) persist the best.
+    The streamed variant runs one block per SM and is timed once (bps 0).
     Returns (best, table) where table maps (wpt, bps) -> ms."""
     table = {}
     for wpt in _b.bsfp_variants_compiled(f, op):
-        for bps in bps_choices:
+        for bps in ((0,) if wpt == _b.VARIANT_STREAMED else bps_choices):
             _b.bsfp_set_variant(f, op, wpt, bps)
             table[(wpt, bps)] = time_op(op, f, a, b, c, out, n, reps)
     best = min(table, key=table.get)

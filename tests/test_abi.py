@@ -88,14 +88,24 @@ def test_status_strings():
 
 def test_variants_and_overrides():
     f = bs.Format(5, 7)
-    assert bs.bsfp_variants_compiled(f, "add") == [1, 2, 4]
-    assert bs.bsfp_variant(f, "add") in (1, 2, 4)
+    assert bs.bsfp_variants_compiled(f, "add") == [1, 2, 4, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variants_compiled(f, "mul") == [1, 2, 4, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variants_compiled(f, "fma2") == [1, 2]
+    assert bs.bsfp_variants_compiled(bs.Format(8, 23), "mul") == [1, 2]
+    assert bs.bsfp_variant(f, "add") in (1, 2, 4, bs.VARIANT_STREAMED)
     g = bs.Format(6, 9)
     assert len(bs.bsfp_variants_compiled(g, "mul")) == 1
     with pytest.raises(bs.BsfpError):
         bs.bsfp_set_variant(g, "mul", 4)
     bs.bsfp_set_variant(f, "mul", 1, 3)
     assert bs.bsfp_variant(f, "mul") == 1
+    bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED, 0)
+    assert bs.bsfp_variant(f, "mul") == bs.VARIANT_STREAMED
+    with pytest.raises(bs.BsfpError):
+        bs.bsfp_set_variant(f, "fma2", bs.VARIANT_STREAMED)
+    for bad in (3, 5, 16):
+        with pytest.raises(bs.BsfpError):
+            bs.bsfp_set_variant(f, "mul", bad)
     bs.bsfp_set_variant(f, "mul", 2, 0)
     assert bs.bsfp_variant(f, "mul") == 2
     # every format in range is compiled for every op

@@ -1,0 +1,164 @@
+"""Parity of the streamed kernels (variant BSFP_VARIANT_STREAMED: a producer
+warp brings the operands' planes into a shared-memory ring with TMA bulk
+copies; consumer warps run the circuits from it) through the C ABI.
+
+The circuits are those of the grid-stride kernels; what is new is the data
+movement -- tiles of TW word columns handed to blocks round-robin, a ring of
+NST stages per block, bounded mbarrier waits.  So the cases are chosen by
+tile geometry: sizes inside one tile, on both sides of a tile boundary, with
+a ragged last tile; and sizes at which every block goes round its ring
+several times.  Small sizes are compared with the oracle element by element
+(whole plane buffers, padding included); the large ones bit for bit with the
+grid-stride kernel over whole plane buffers and with the oracle on sampled
+elements.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_1602_04716_gb300 as bs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+STREAM_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
+MODES = [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ]
+OPS = ["add", "sub", "mul"]
+
+
+def shape(E, M):
+    """(tile words per plane, ring stages) of the streamed kernel."""
+    B = 1 + E + M
+    nc = 16 if B <= 9 else (15 if B <= 13 else 12)
+    return 32 * nc * 2, (3 if B <= 9 else 2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    bs.bsfp_fault_status(clear=True)
+    yield
+    torch.cuda.synchronize()
+    for E, M in STREAM_FORMATS:
+        for rnd in MODES:
+            for op in OPS:
+                bs.bsfp_set_variant(bs.Format(E, M, rnd), op, 0, 0)
+
+
+def dev(x: np.ndarray):
+    x = np.ascontiguousarray(x)
+    view = {1: np.uint8, 2: np.int16, 4: np.int32}[x.dtype.itemsize]
+    return torch.from_numpy(x.view(view).copy()).cuda()
+
+
+def test_streamed_variant_is_compiled_where_documented():
+    for E, M in STREAM_FORMATS:
+        for rnd in MODES:
+            f = bs.Format(E, M, rnd)
+            for op in OPS:
+                assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(f, op), (E, M, rnd, op)
+            for op in ("fma2", "div"):
+                assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(f, op)
+    for E, M in [(8, 23), (6, 9), (3, 2)]:
+        assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(bs.Format(E, M), "mul")
+    with pytest.raises(bs.BsfpError):
+        bs.bsfp_set_variant(bs.Format(6, 9), "mul", bs.VARIANT_STREAMED)
+
+
+@pytest.mark.parametrize("E,M", STREAM_FORMATS)
+@pytest.mark.parametrize("rnd", MODES)
+def test_tile_geometry_vs_oracle(E, M, rnd):
+    """n inside the first tile, either side of the first tile boundary, and
+    three tiles plus a ragged tail; every word of every output plane
+    (padding included) against the oracle."""
+    B = 1 + E + M
+    TW, _ = shape(E, M)
+    f = bs.Format(E, M, rnd)
+    for n in (1, 33, 32 * TW - 1, 32 * TW + 1, 3 * 32 * TW + 77):
+        a = synth.fp_values(E, M, n, 501 + n % 7).astype(np.uint32)
+        b = synth.fp_values(E, M, n, 601 + n % 5).astype(np.uint32)
+        pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+        for op in OPS:
+            bs.bsfp_set_variant(f, op, bs.VARIANT_STREAMED)
+            assert bs.bsfp_variant(f, op) == bs.VARIANT_STREAMED
+            out = torch.full_like(pa, -1)
+            bs.bsfp_op(op, f, pa, pb, out, n)
+            got = out.cpu().numpy().view(np.uint32).reshape(B, -1)
+            want = oracle.pack(B, oracle.binop(op, E, M, rnd, a, b))
+            assert (got == want).all(), "%s 1/%d/%d rnd=%d n=%d" % (op, E, M, rnd, n)
+    assert bs.bsfp_fault_status() == 0
+
+
+@pytest.mark.parametrize("E,M", STREAM_FORMATS)
+def test_several_rounds_of_the_ring(E, M):
+    """Every block takes NST + 2 tiles (the refill path of the ring) and the
+    last tile is ragged: the streamed and grid-stride kernels agree on every
+    word of the output planes, and 4,096 sampled elements plus the tail agree
+    with the oracle, in all four modes."""
+    B = 1 + E + M
+    TW, NST = shape(E, M)
+    n = bs.bsfp_num_sms() * (NST + 2) * 32 * TW - 3 * 32 * TW // 2 + 12345
+    cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[bs.bsfp_container_bytes(bs.Format(E, M))]
+    std = bs.empty_standard(bs.Format(E, M), n)
+    planes = []
+    for seed in (7001, 7002):
+        bs.bsfp_synth_fp_values(bs.Format(E, M), n, seed, 0, 0, std)
+        p = bs.empty_bitslice(bs.Format(E, M), n)
+        bs.bsfp_pack(bs.Format(E, M), std, n, p)
+        planes.append(p)
+    rng = np.random.default_rng(E * 64 + M)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 4096), np.arange(n - 64, n)])).astype(np.int64)
+    xa = synth.fp_values_at(E, M, idx, 7001)
+    xb = synth.fp_values_at(E, M, idx, 7002)
+    idx_t = torch.from_numpy(idx).cuda()
+    ref = bs.empty_bitslice(bs.Format(E, M), n)
+    got = bs.empty_bitslice(bs.Format(E, M), n)
+    for rnd in MODES:
+        f = bs.Format(E, M, rnd)
+        for op in OPS:
+            bs.bsfp_set_variant(f, op, bs.bsfp_variants_compiled(f, op)[0])
+            bs.bsfp_op(op, f, planes[0], planes[1], ref, n)
+            bs.bsfp_set_variant(f, op, bs.VARIANT_STREAMED)
+            got.fill_(-1)
+            bs.bsfp_op(op, f, planes[0], planes[1], got, n)
+            assert torch.equal(got, ref), "%s 1/%d/%d rnd=%d: streamed != grid-stride" % (op, E, M, rnd)
+            bs.bsfp_unpack(f, got, n, std)
+            res = std[idx_t].cpu().numpy().view(cdt).astype(np.uint32)
+            want = oracle.binop(op, E, M, rnd, xa, xb)
+            bad = np.nonzero(res != want)[0]
+            assert not len(bad), "%s 1/%d/%d rnd=%d: %d bad, first idx %d" % (op, E, M, rnd, len(bad), idx[bad[0]])
+    assert bs.bsfp_fault_status() == 0
+    del planes, ref, got, std
+    torch.cuda.empty_cache()
+
+
+def test_streamed_writes_nothing_outside_its_output():
+    """Guard words of 4 KiB on both sides of the output planes survive a
+    streamed launch whose last tile is ragged."""
+    E, M = 5, 7
+    B = 1 + E + M
+    f = bs.Format(E, M)
+    TW, _ = shape(E, M)
+    n = 5 * 32 * TW + 1000
+    S = bs.bsfp_plane_stride(n)
+    a = synth.fp_values(E, M, n, 11).astype(np.uint32)
+    b = synth.fp_values(E, M, n, 12).astype(np.uint32)
+    pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+    G = 1024
+    buf = torch.full((B * S + 2 * G,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    out = buf[G:G + B * S]
+    for op in OPS:
+        bs.bsfp_set_variant(f, op, bs.VARIANT_STREAMED)
+        bs.bsfp_op(op, f, pa, pb, out, n)
+        torch.cuda.synchronize()
+        assert bool((buf[:G] == 0x5A5A5A5A).all()) and bool((buf[G + B * S:] == 0x5A5A5A5A).all()), op
+        want = oracle.pack(B, oracle.binop(op, E, M, 0, a, b))
+        assert (out.cpu().numpy().view(np.uint32).reshape(B, -1) == want).all(), op
+
+
+def test_fault_word_is_clear_after_the_streamed_runs():
+    assert bs.bsfp_fault_status(clear=True) == 0
+    assert bs.bsfp_fault_status() == 0
