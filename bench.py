@@ -51,7 +51,13 @@ WORKLOAD = ("plain single-format at scale: bs_add + bs_mul (RN) on 1/4/4 and 1/5
 # by (E, M, op), from the ncu capture of the kernel as it now stands at 2^26
 # elements scaled by 4 (profiles/binop_1_5_7_add_mul_full_2p26.md); a kernel
 # not listed, or changed since its capture, reports null.
-NCU_TRAFFIC = {(5, 7, "mul"): (218.150656e6 + 70.085376e6) * 4, (5, 7, "add"): (218.121216e6 + 71.256576e6) * 4}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from ncu captures at 2^26 elements
+# scaled x4 to the 2^28-element launch, keyed by (E, M, op, kernel variant): a figure stands only
+# for the kernel it was taken on (profiles/stream_mul_1_5_7_full_2p26.md,
+# profiles/binop_1_5_7_add_mul_full_2p26.md).
+NCU_TRAFFIC = {(5, 7, "mul", 8): (218.138112e6 + 67.741440e6) * 4,
+               (5, 7, "mul", 4): (218.150656e6 + 70.085376e6) * 4,
+               (5, 7, "add", 2): (218.121216e6 + 71.256576e6) * 4}
 
 
 def apply_tuning() -> int:
@@ -311,7 +317,7 @@ def run_gpu(args):
         roof = {"bound": "alu", "achieved": d["logic_tops"], "peak": L / 1e12, "unit": "Tops/s",
                 "frac": d["logic_tops"] * 1e12 / L,
                 "peak_source": "measured LOP3 issue rate (bsfp_lop3_probe, this run)"}
-    tr = NCU_TRAFFIC.get((E, M, op)) if n == N else None
+    tr = NCU_TRAFFIC.get((E, M, op, d["wpt"])) if n == N else None
     roof.update({"kernel": d["kernel"], "traffic": tr,
                  "algorithmic_bytes": 3 * B * n / 8, "gate_ops": d["gates_per_word"] * ((n + 31) // 32),
                  "hbm_peak_gbs": hbm, "logic_peak_tops": L / 1e12})
