@@ -5,7 +5,9 @@
  * The circuits are written once, as the templates of circuit.cuh.  Recorded
  * by netlist.h they become netlists in which every gate is a function of at
  * most three words with its truth table, inversions absorbed, constants
- * folded, identical gates shared and dead gates dropped -- G gates in all.
+ * folded, identical gates shared and dead gates dropped, and then re-covered
+ * by 3-input functions (lut3_map in netlist.h), which merges a gate into its
+ * user wherever the two read at most three values -- G gates in all.
  * Left to the compiler, the same templates become more instructions than
  * that, because it re-derives its own 3-input groupings from the and/or/xor
  * expressions (a majority gate that shares x^y with the neighbouring sum, for
@@ -58,9 +60,12 @@ std::string value_name(int32_t ref, int B) {
 template <int E, int M, int R, int OP>
 void emit(FILE* f, int opc) {
     constexpr int B = 1 + E + M;
+    Graph rec;
+    GW rr[B];
+    record<E, M, R, OP>(rec, rr);
     Graph g;
     GW r[B];
-    record<E, M, R, OP>(g, r);
+    lut3_map(rec, rr, B, g, r);
     const std::vector<char> live = live_set(g, r, B);
     long n = 0;
     for (char m : live) n += m;

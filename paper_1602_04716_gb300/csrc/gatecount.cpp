@@ -20,10 +20,11 @@ namespace {
 
 template <int E, int M, int R, int OP> static long count_one() {
     constexpr int B = 1 + E + M;
-    Graph g;
-    GW r[B];
+    Graph g, mg;
+    GW r[B], mr[B];
     record<E, M, R, OP>(g, r);
-    return count_live(g, r, B);
+    lut3_map(g, r, B, mg, mr);
+    return count_live(mg, mr, B);
 }
 
 template <int E, int M, int OP> static long count_op(int rnd) {

@@ -8,14 +8,16 @@
  * most three words given by its truth table (one LOP3 on sm_103a).  The
  * recorder absorbs inversions into the truth table, folds constants and
  * repeated inputs, shares identical gates, and the live set keeps only the
- * gates that reach an output.  gatecount.cpp counts the live gates;
- * circuitgen.cpp prints them as device code.
+ * gates that reach an output.  lut3_map then re-covers the live netlist by
+ * 3-input functions.  gatecount.cpp counts the mapped gates; circuitgen.cpp
+ * prints them as device code.
  *
  * Each translation unit that includes this header gets its own recorder.
  */
 #pragma once
 #include <stdint.h>
 
+#include <algorithm>
 #include <unordered_map>
 #include <vector>
 
@@ -195,6 +197,273 @@ static long count_live(const Graph& g, const GW* out, int nout) {
     long n = 0;
     for (char m : live_set(g, out, nout)) n += m;
     return n;
+}
+
+/* ------------------------------------------------------ LUT3 re-mapping --- *
+ * The recorder keeps the gates in the grouping the templates wrote them in.
+ * A gate whose only use is a neighbouring gate can often be merged into it:
+ * the pair is one 3-input function whenever the two together read at most
+ * three distinct values (a partial product AND feeding a half adder's XOR,
+ * say).  lut3_map covers the live netlist with 3-input functions by cut
+ * enumeration: every gate's 3-feasible cuts (sets of at most three values
+ * that determine it) are merged from its inputs' cuts, a cover is chosen by
+ * area flow (each value's cost shared among its uses), then refined by exact
+ * local area (the gates a choice adds to or removes from the cover), and
+ * each chosen cut becomes one gate whose truth table is that of the cone
+ * over the cut.  Inputs, outputs and the function computed are unchanged;
+ * only gates disappear. */
+namespace lut3 {
+
+constexpr int MAX_CUTS = 48;
+
+struct Cut {
+    int n = 0;
+    int32_t leaf[3];   /* value ids, ascending */
+};
+
+static inline bool cut_subset(const Cut& a, const Cut& b) {   /* a within b */
+    for (int i = 0; i < a.n; ++i) {
+        bool f = false;
+        for (int j = 0; j < b.n; ++j) f |= a.leaf[i] == b.leaf[j];
+        if (!f) return false;
+    }
+    return true;
+}
+
+static inline bool cut_merge(const Cut& a, const Cut& b, Cut* o) {
+    int i = 0, j = 0, n = 0;
+    while (i < a.n || j < b.n) {
+        int32_t v;
+        if (j >= b.n || (i < a.n && a.leaf[i] < b.leaf[j])) v = a.leaf[i++];
+        else if (i >= a.n || b.leaf[j] < a.leaf[i]) v = b.leaf[j++];
+        else { v = a.leaf[i]; ++i; ++j; }
+        if (n == 3) return false;
+        o->leaf[n++] = v;
+    }
+    o->n = n;
+    return true;
+}
+
+struct Mapper {
+    const Graph& g;
+    int first;                                  /* id of the first gate */
+    std::vector<char> live;
+    std::vector<std::vector<Cut>> cuts;         /* per gate index */
+    std::vector<int> best;                      /* chosen cut per gate index */
+    std::vector<int> refs;                      /* per value id: uses in the current cover */
+    std::vector<double> flow;                   /* area flow per value id */
+
+    explicit Mapper(const Graph& gr) : g(gr), first(gr.ninputs + 1) {}
+
+    bool is_gate(int32_t id) const { return id >= first; }
+    int fanins(int idx, int32_t* f) const {
+        int n = 0;
+        for (int k = 0; k < 3; ++k) {
+            const int32_t r = g.in[k][idx];
+            if (r < 0) continue;
+            const int32_t id = r >> 1;
+            if (id == 0) continue;   /* constants are folded into the truth tables */
+            bool dup = false;
+            for (int q = 0; q < n; ++q) dup |= f[q] == id;
+            if (!dup) f[n++] = id;
+        }
+        return n;
+    }
+
+    void enumerate() {
+        const size_t ng = g.lut.size();
+        cuts.assign(ng, {});
+        for (size_t idx = 0; idx < ng; ++idx) {
+            if (!live[idx]) continue;
+            int32_t f[3];
+            const int nf = fanins((int)idx, f);
+            /* candidate cut sets of each fanin: its own trivial cut, plus its cuts if a gate */
+            std::vector<Cut> lists[3];
+            for (int q = 0; q < nf; ++q) {
+                Cut t;
+                t.n = 1;
+                t.leaf[0] = f[q];
+                lists[q].push_back(t);
+                if (is_gate(f[q]))
+                    for (const Cut& c : cuts[f[q] - first]) lists[q].push_back(c);
+            }
+            std::vector<Cut> out;
+            Cut acc;
+            acc.n = 0;
+            combine(lists, nf, 0, acc, out);
+            /* drop dominated cuts, keep the smallest first */
+            std::sort(out.begin(), out.end(), [](const Cut& a, const Cut& b) {
+                if (a.n != b.n) return a.n < b.n;
+                for (int i = 0; i < a.n; ++i)
+                    if (a.leaf[i] != b.leaf[i]) return a.leaf[i] < b.leaf[i];
+                return false;
+            });
+            std::vector<Cut> keep;
+            for (const Cut& c : out) {
+                bool dom = false;
+                for (const Cut& k : keep) dom |= cut_subset(k, c);
+                if (!dom) keep.push_back(c);
+                if ((int)keep.size() >= MAX_CUTS) break;
+            }
+            cuts[idx] = keep;
+        }
+    }
+
+    void combine(const std::vector<Cut>* lists, int nf, int q, const Cut& acc, std::vector<Cut>& out) {
+        if (q == nf) {
+            out.push_back(acc);
+            return;
+        }
+        for (const Cut& c : lists[q]) {
+            Cut m;
+            if (cut_merge(acc, c, &m)) combine(lists, nf, q + 1, m, out);
+        }
+    }
+
+    /* area-flow selection in topological order */
+    void select_flow(const std::vector<int>& fanout) {
+        const size_t ng = g.lut.size();
+        flow.assign(first + ng, 0.0);
+        best.assign(ng, -1);
+        for (size_t idx = 0; idx < ng; ++idx) {
+            if (!live[idx]) continue;
+            double bv = 1e300;
+            int bi = -1;
+            for (int ci = 0; ci < (int)cuts[idx].size(); ++ci) {
+                const Cut& c = cuts[idx][ci];
+                double v = 1.0;
+                for (int i = 0; i < c.n; ++i) {
+                    const int32_t l = c.leaf[i];
+                    v += flow[l] / (fanout[l] > 0 ? fanout[l] : 1);
+                }
+                if (v < bv - 1e-9) {
+                    bv = v;
+                    bi = ci;
+                }
+            }
+            best[idx] = bi;
+            flow[first + idx] = bv;
+        }
+    }
+
+    int deref(int idx) {   /* gates freed by dropping gate idx's cut */
+        int a = 1;
+        const Cut& c = cuts[idx][best[idx]];
+        for (int i = 0; i < c.n; ++i) {
+            const int32_t l = c.leaf[i];
+            if (is_gate(l) && --refs[l] == 0) a += deref(l - first);
+        }
+        return a;
+    }
+    int ref(int idx) {     /* gates added by taking gate idx's cut */
+        int a = 1;
+        const Cut& c = cuts[idx][best[idx]];
+        for (int i = 0; i < c.n; ++i) {
+            const int32_t l = c.leaf[i];
+            if (is_gate(l) && refs[l]++ == 0) a += ref(l - first);
+        }
+        return a;
+    }
+
+    /* reference counts of the cover reachable from the outputs */
+    void count_cover(const GW* out, int nout) {
+        refs.assign(first + g.lut.size(), 0);
+        for (int i = 0; i < nout; ++i) {
+            const int32_t id = out[i].ref >> 1;
+            if (is_gate(id) && refs[id]++ == 0) ref(id - first);
+        }
+    }
+
+    void refine(const GW* out, int nout, int rounds) {
+        for (int r = 0; r < rounds; ++r) {
+            count_cover(out, nout);
+            for (size_t idx = 0; idx < g.lut.size(); ++idx) {
+                if (!live[idx] || refs[first + idx] == 0) continue;
+                const int a0 = deref((int)idx);
+                int bi = best[idx], ba = a0;
+                for (int ci = 0; ci < (int)cuts[idx].size(); ++ci) {
+                    best[idx] = ci;
+                    const int a = ref((int)idx);
+                    deref((int)idx);
+                    if (a < ba) {
+                        ba = a;
+                        bi = ci;
+                    }
+                }
+                best[idx] = bi;
+                ref((int)idx);
+            }
+        }
+        count_cover(out, nout);
+    }
+
+    /* truth table (8 bits, leaves on a = 0xF0, b = 0xCC, c = 0xAA) of value id over a cut */
+    unsigned cone(int32_t id, const Cut& c, std::unordered_map<int32_t, unsigned>& memo) const {
+        static const unsigned pat[3] = {0xF0u, 0xCCu, 0xAAu};
+        for (int i = 0; i < c.n; ++i)
+            if (c.leaf[i] == id) return pat[i];
+        if (id == 0) return 0u;
+        auto it = memo.find(id);
+        if (it != memo.end()) return it->second;
+        const int idx = id - first;
+        unsigned v[3] = {0u, 0u, 0u};
+        for (int k = 0; k < 3; ++k) {
+            const int32_t r = g.in[k][idx];
+            if (r >= 0) v[k] = cone(r >> 1, c, memo) ^ ((r & 1) ? 0xFFu : 0u);
+        }
+        unsigned t = 0u;
+        const unsigned L = g.lut[idx];
+        for (int i = 0; i < 8; ++i)
+            if ((L >> i) & 1u)
+                t |= ((i & 4) ? v[0] : ~v[0]) & ((i & 2) ? v[1] : ~v[1]) & ((i & 1) ? v[2] : ~v[2]);
+        t &= 0xFFu;
+        memo.emplace(id, t);
+        return t;
+    }
+};
+
+}  // namespace lut3
+
+/* Re-map g's live netlist (outputs out[0..nout)) into ng; mapped[i] are the
+ * outputs in ng.  ng has the same inputs. */
+static void lut3_map(const Graph& g, const GW* out, int nout, Graph& ng, GW* mapped) {
+    lut3::Mapper m(g);
+    m.live = live_set(g, out, nout);
+    const int first = g.ninputs + 1;
+    /* fanout of every value among live gates and outputs */
+    std::vector<int> fanout(first + g.lut.size(), 0);
+    for (size_t idx = 0; idx < g.lut.size(); ++idx) {
+        if (!m.live[idx]) continue;
+        int32_t f[3];
+        const int nf = m.fanins((int)idx, f);
+        for (int q = 0; q < nf; ++q) ++fanout[f[q]];
+    }
+    for (int i = 0; i < nout; ++i) ++fanout[out[i].ref >> 1];
+    m.enumerate();
+    m.select_flow(fanout);
+    m.refine(out, nout, 4);
+    /* rebuild: every gate in the cover becomes one recorded gate */
+    ng = Graph();
+    ng.ninputs = g.ninputs;
+    Graph* saved = g_graph;
+    g_graph = &ng;
+    std::vector<GW> newref(first + g.lut.size());
+    for (int32_t id = 0; id < first; ++id) newref[id] = GW(id << 1, 0);
+    for (size_t idx = 0; idx < g.lut.size(); ++idx) {
+        const int32_t id = first + (int32_t)idx;
+        if (!m.live[idx] || m.refs[id] == 0) continue;
+        const lut3::Cut& c = m.cuts[idx][m.best[idx]];
+        std::unordered_map<int32_t, unsigned> memo;
+        const unsigned L = m.cone(id, c, memo);
+        GW x[3] = {GW(0u), GW(0u), GW(0u)};
+        for (int i = 0; i < c.n; ++i) x[i] = newref[c.leaf[i]];
+        newref[id] = lop(L, x[0], x[1], x[2]);
+    }
+    for (int i = 0; i < nout; ++i) {
+        const GW v = newref[out[i].ref >> 1];
+        mapped[i] = GW(v.ref ^ (out[i].ref & 1), 0);
+    }
+    g_graph = saved;
 }
 
 /* Record fp_op<E, M, R, OP> (R: rounding mode, bit 0 toward zero, bit 1
