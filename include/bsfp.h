@@ -415,6 +415,16 @@ int32_t bsfp_variants_compiled(bsfp_format f, int32_t op);
  * uncompiled variant.  Not synchronised with launches already queued: it
  * affects later calls. */
 bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blocks_per_sm);
+/* The variant a call of (format, op) on n elements launches: the one
+ * bsfp_variant reports, except that the streamed variant gives way to the
+ * default grid-stride variant when the call has fewer than
+ * tiles_per_sm x SMs tiles of the streamed kernel (its ring would never
+ * fill).  -1 on a bad argument, 0 if the format is not compiled.  Needs the
+ * device only for its SM count. */
+int32_t bsfp_variant_for(bsfp_format f, int32_t op, int64_t n);
+/* Minimum tiles per SM for the streamed variant (default 2; 0 = always take
+ * it when selected).  Process-wide; BSFP_ERR_SIZE outside [0, 1024]. */
+bsfp_status bsfp_set_stream_min_tiles(int32_t tiles_per_sm);
 /* Kernel launches this library has issued on this process so far. */
 int64_t bsfp_launch_count(void);
 /* Fault word of the current device: 0 if no kernel has reported a fault,

@@ -130,6 +130,8 @@ def _lib():
                 "bsfp_set_variant": (i32, [F, i32, i32, i32]),
                 "bsfp_launch_count": (i64, []),
                 "bsfp_fault_status": (i32, [i32]),
+                "bsfp_variant_for": (i32, [F, i32, i64]),
+                "bsfp_set_stream_min_tiles": (i32, [i32]),
                 "bsfp_synth_fp_values": (i32, [F, i64, u64, u64, i64, p, p]),
                 "bsfp_lop3_probe": (i32, [p, i32, i32, i32, u32, p]),
                 "bsfp_num_sms": (i32, []),
@@ -318,6 +320,15 @@ def bsfp_variants_compiled(f, op) -> list:
     grid-stride kernel and VARIANT_STREAMED (8) for the streamed kernel."""
     m = int(_lib().bsfp_variants_compiled(_fmt(f), OPS.get(op, op)))
     return [w for i, w in enumerate((1, 2, 4, VARIANT_STREAMED)) if m > 0 and (m >> i) & 1]
+
+
+def bsfp_variant_for(f, op, n: int) -> int:
+    """The variant a call of (f, op) on n elements launches."""
+    return int(_lib().bsfp_variant_for(_fmt(f), OPS.get(op, op), n))
+
+
+def bsfp_set_stream_min_tiles(tiles_per_sm: int):
+    _check(_lib().bsfp_set_stream_min_tiles(tiles_per_sm), "bsfp_set_stream_min_tiles")
 
 
 def bsfp_fault_status(clear: bool = False) -> int:

@@ -62,6 +62,11 @@ static void init_tables() {
     register_stream_e5_m10(); register_stream_e8_m7();
 }
 
+/* The streamed kernel is taken only when every SM gets at least this many
+ * tiles: with fewer, its ring never fills and the grid-stride kernel is
+ * faster (bsfp_set_stream_min_tiles). */
+static std::atomic<int32_t> g_stream_min_tiles{2};
+
 /* Devices on which a streamed kernel has opted in to its shared memory, one
  * bit per device, per (E, M, rounding, op class). */
 static std::atomic<uint64_t> g_stream_ready[TAB_E][TAB_M][TAB_R][OPC_ALL];
@@ -193,6 +198,11 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
         std::lock_guard<std::mutex> lk(g_shape_mu);
         const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
         wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
+        if (wpt == VARIANT_STREAMED) {
+            const int64_t tiles = (p.S + e->stream_tw - 1) / e->stream_tw;
+            if (tiles < (int64_t)g_stream_min_tiles.load(std::memory_order_relaxed) * device_num_sms())
+                wpt = e->default_wpt;
+        }
         if (wpt == VARIANT_STREAMED) {
             bps = 1;
         } else {
@@ -483,6 +493,32 @@ int32_t bsfp_variants_compiled(bsfp_format f, int32_t op) {
     if (!format_ok(f) || opclass(op) < 0) return -1;
     const BinopEntry* e = entry_for(f, opclass(op));
     return e ? (int32_t)e->wpt_mask : 0;
+}
+
+bsfp_status bsfp_set_stream_min_tiles(int32_t tiles_per_sm) {
+    if (tiles_per_sm < 0 || tiles_per_sm > 1024) return BSFP_ERR_SIZE;
+    g_stream_min_tiles.store(tiles_per_sm, std::memory_order_relaxed);
+    return BSFP_OK;
+}
+
+int32_t bsfp_variant_for(bsfp_format f, int32_t op, int64_t n) {
+    if (!format_ok(f) || opclass(op) < 0 || n < 0 || n > BSFP_MAX_N) return -1;
+    const int opc = opclass(op);
+    const BinopEntry* e = entry_for(f, opc);
+    if (!e) return 0;
+    int wpt;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+        wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
+    }
+    if (wpt == VARIANT_STREAMED) {
+        const int64_t S = bsfp_plane_stride(n);
+        const int64_t tiles = (S + e->stream_tw - 1) / e->stream_tw;
+        if (tiles < (int64_t)g_stream_min_tiles.load(std::memory_order_relaxed) * device_num_sms())
+            wpt = e->default_wpt;
+    }
+    return wpt;
 }
 
 int32_t bsfp_variant(bsfp_format f, int32_t op) {

@@ -86,6 +86,19 @@ def test_status_strings():
     assert bs.status_str(-100) == "unknown status"
 
 
+def test_stream_threshold_and_variant_query_arguments():
+    L = _binding._lib()
+    assert L.bsfp_set_stream_min_tiles(-1) == bs.ERR_SIZE
+    assert L.bsfp_set_stream_min_tiles(1025) == bs.ERR_SIZE
+    assert L.bsfp_set_stream_min_tiles(2) == bs.OK
+    assert bs.bsfp_variant_for(bs.Format(9, 7), "mul", 10) == -1
+    assert bs.bsfp_variant_for(bs.Format(5, 7), 9, 10) == -1
+    assert bs.bsfp_variant_for(bs.Format(5, 7), "mul", -1) == -1
+    bs.bsfp_set_variant(bs.Format(5, 7), "mul", 2, 0)
+    assert bs.bsfp_variant_for(bs.Format(5, 7), "mul", 1 << 20) == 2
+    bs.bsfp_set_variant(bs.Format(5, 7), "mul", 0, 0)
+
+
 def test_variants_and_overrides():
     f = bs.Format(5, 7)
     assert bs.bsfp_variants_compiled(f, "add") == [1, 2, 4, bs.VARIANT_STREAMED]

@@ -40,7 +40,9 @@ def _cuda():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     torch.cuda.set_device(0)
     bs.bsfp_fault_status(clear=True)
+    bs.bsfp_set_stream_min_tiles(0)   # take the streamed kernel at every size
     yield
+    bs.bsfp_set_stream_min_tiles(2)
     torch.cuda.synchronize()
     for E, M in STREAM_FORMATS:
         for rnd in MODES:
@@ -162,3 +164,23 @@ def test_streamed_writes_nothing_outside_its_output():
 def test_fault_word_is_clear_after_the_streamed_runs():
     assert bs.bsfp_fault_status(clear=True) == 0
     assert bs.bsfp_fault_status() == 0
+
+
+def test_small_calls_fall_back_to_the_grid_stride_kernel():
+    """With the default threshold (2 tiles per SM) a call too small to fill
+    the ring runs the default grid-stride variant; results do not change."""
+    E, M = 5, 7
+    f = bs.Format(E, M)
+    TW, _ = shape(E, M)
+    sms = bs.bsfp_num_sms()
+    bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED)
+    try:
+        bs.bsfp_set_stream_min_tiles(2)
+        small, big = 32 * TW * sms, 2 * 32 * TW * sms
+        assert bs.bsfp_variant_for(f, "mul", small) not in (bs.VARIANT_STREAMED, 0, -1)
+        assert bs.bsfp_variant_for(f, "mul", big) == bs.VARIANT_STREAMED
+        bs.bsfp_set_stream_min_tiles(0)
+        assert bs.bsfp_variant_for(f, "mul", 1) == bs.VARIANT_STREAMED
+    finally:
+        bs.bsfp_set_stream_min_tiles(0)
+        bs.bsfp_set_variant(f, "mul", 0, 0)
