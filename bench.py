@@ -157,9 +157,26 @@ def cpu_baseline(target_s: float = 12.0):
                 tot += time.perf_counter() - t
                 els += m
         passes += 1
-    return {"value": els / tot, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same oracle on one core, over the first 2^22 elements of each vector
+    m1 = min(m, 1 << 22)
+    oracle.set_threads(1)
+    try:
+        t1, els1 = 0.0, 0
+        for E, M in FORMATS:
+            a, b = data[(E, M)]
+            for op in OPS:
+                t = time.perf_counter()
+                oracle.binop(op, E, M, RND, a[:m1], b[:m1])
+                t1 += time.perf_counter() - t
+                els1 += m1
+    finally:
+        oracle.set_threads(cores)
+    return {"value": els / tot, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d elements of each of the 4 (format, op) vectors of the workload (same seeds), "
-                      "%d passes, %.1f s of oracle time" % (m, passes, tot)}
+                      "%d passes, %.1f s of oracle time" % (m, passes, tot),
+            "single_core": {"value": els1 / t1, "unit": UNIT, "cores": 1,
+                            "sample": "first %d elements of each of the 4 vectors, one pass, %.1f s" % (m1, t1)}}
 
 
 def run_reference(args):

@@ -77,6 +77,8 @@ def lib():
             L.oracle_unpack.restype = None
             L.oracle_num_threads.argtypes = []
             L.oracle_num_threads.restype = i32
+            L.oracle_set_threads.argtypes = [i32]
+            L.oracle_set_threads.restype = None
             _lib = L
     return _lib
 
@@ -171,3 +173,8 @@ def unpack(B: int, planes, n: int) -> np.ndarray:
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+def set_threads(k: int) -> None:
+    """Threads of the following oracle calls (k > 0)."""
+    lib().oracle_set_threads(int(k))

@@ -420,3 +420,14 @@ int oracle_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads for the following calls (the CPU baseline is timed at one core
+ * and at all cores); k <= 0 is ignored. */
+void oracle_set_threads(int k) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
