@@ -422,6 +422,18 @@ bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blo
  * fill).  -1 on a bad argument, 0 if the format is not compiled.  Needs the
  * device only for its SM count. */
 int32_t bsfp_variant_for(bsfp_format f, int32_t op, int64_t n);
+/* Self-test of the streamed kernel's bounded waits: runs (format, op) on a,
+ * b -> out (n elements) with the streamed kernel, but issues no copies for
+ * tile withhold_tile (0 <= tile < number of tiles; -1 withholds none), and
+ * bounds every wait at wait_cycles SM cycles (2^16 .. 2^34).  The waits on
+ * the withheld tile run out, the block stops after letting its other copies
+ * land, and the fault word (bsfp_fault_status) becomes 1; the output of the
+ * blocks that stopped is incomplete, the device stays usable.  For tests of
+ * the failure path; no counterpart in the paper.  BSFP_ERR_UNSUPPORTED if
+ * (format, op) has no streamed kernel; BSFP_ERR_SIZE for an out-of-range
+ * tile or bound. */
+bsfp_status bsfp_stream_selftest(bsfp_format f, int32_t op, const uint32_t* a, const uint32_t* b, uint32_t* out,
+                                 int64_t n, int64_t withhold_tile, int64_t wait_cycles, cudaStream_t s);
 /* Minimum tiles per SM for the streamed variant (default 2; 0 = always take
  * it when selected).  Process-wide; BSFP_ERR_SIZE outside [0, 1024]. */
 bsfp_status bsfp_set_stream_min_tiles(int32_t tiles_per_sm);

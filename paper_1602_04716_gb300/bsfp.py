@@ -132,6 +132,7 @@ def _lib():
                 "bsfp_fault_status": (i32, [i32]),
                 "bsfp_variant_for": (i32, [F, i32, i64]),
                 "bsfp_set_stream_min_tiles": (i32, [i32]),
+                "bsfp_stream_selftest": (i32, [F, i32, p, p, p, i64, i64, i64, p]),
                 "bsfp_synth_fp_values": (i32, [F, i64, u64, u64, i64, p, p]),
                 "bsfp_lop3_probe": (i32, [p, i32, i32, i32, u32, p]),
                 "bsfp_num_sms": (i32, []),
@@ -325,6 +326,13 @@ def bsfp_variants_compiled(f, op) -> list:
 def bsfp_variant_for(f, op, n: int) -> int:
     """The variant a call of (f, op) on n elements launches."""
     return int(_lib().bsfp_variant_for(_fmt(f), OPS.get(op, op), n))
+
+
+def bsfp_stream_selftest(f, op, a, b, out, n: int, withhold_tile: int, wait_cycles: int, stream=None):
+    """Streamed kernel with one tile's copies withheld and a short wait bound
+    (the failure path of its bounded waits)."""
+    _check(_lib().bsfp_stream_selftest(_fmt(f), OPS.get(op, op), _ptr(a), _ptr(b), _ptr(out), n, withhold_tile,
+                                       wait_cycles, _stream(stream)), "bsfp_stream_selftest")
 
 
 def bsfp_set_stream_min_tiles(tiles_per_sm: int):

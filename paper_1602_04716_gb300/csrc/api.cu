@@ -20,6 +20,7 @@
 #include "bsfp.h"
 #include "convert.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace bsfp {
 
@@ -188,6 +189,8 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
     p.nwords = (n + 31) / 32;
     p.tailmask = (n % 32) ? ((1u << (n % 32)) - 1u) : ~0u;
     p.negb = (op == BSFP_OP_SUB) ? ~0u : 0u;
+    p.wait_cycles = STREAM_WAIT_CYCLES;
+    p.withhold_tile = -1;
     po->entry = e;
     po->opc = opc;
 
@@ -493,6 +496,41 @@ int32_t bsfp_variants_compiled(bsfp_format f, int32_t op) {
     if (!format_ok(f) || opclass(op) < 0) return -1;
     const BinopEntry* e = entry_for(f, opclass(op));
     return e ? (int32_t)e->wpt_mask : 0;
+}
+
+bsfp_status bsfp_stream_selftest(bsfp_format f, int32_t op, const uint32_t* a, const uint32_t* b, uint32_t* out,
+                                 int64_t n, int64_t withhold_tile, int64_t wait_cycles, cudaStream_t s) {
+    if (wait_cycles < (1ll << 16) || wait_cycles > (1ll << 34)) return BSFP_ERR_SIZE;
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    const int opc = opclass(op);
+    if (opc != OPC_ADDSUB && opc != OPC_MUL) return BSFP_ERR_UNSUPPORTED;
+    if (n <= 0) return BSFP_ERR_SIZE;
+    const BinopEntry* e = entry_for(f, opc);
+    if (!e || !(e->wpt_mask & (unsigned)VARIANT_STREAMED)) return BSFP_ERR_UNSUPPORTED;
+    /* run the streamed kernel whatever the shape settings and size */
+    Shape saved;
+    int32_t min_tiles;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        saved = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+        g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = Shape{(int8_t)VARIANT_STREAMED, 0};
+    }
+    min_tiles = g_stream_min_tiles.exchange(0);
+    PreparedOp po;
+    bsfp_status st = prepare_binop(f, op, a, b, nullptr, out, n, &po);
+    g_stream_min_tiles.store(min_tiles);
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = saved;
+    }
+    if (st != BSFP_OK) return st;
+    const int64_t tiles = (po.args.S + e->stream_tw - 1) / e->stream_tw;
+    if (po.wpt != VARIANT_STREAMED || withhold_tile < -1 || withhold_tile >= tiles) return BSFP_ERR_SIZE;
+    po.args.withhold_tile = withhold_tile;
+    po.args.wait_cycles = wait_cycles;
+    st = launch_prepared(po, s);
+    if (st == BSFP_OK) count_launches(1);
+    return st;
 }
 
 bsfp_status bsfp_set_stream_min_tiles(int32_t tiles_per_sm) {

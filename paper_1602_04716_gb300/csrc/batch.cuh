@@ -104,6 +104,8 @@ __global__ void __launch_bounds__(128) batch_kernel(const JobDesc* __restrict__ 
         p.tailmask = d.tailmask;
         p.negb = d.negb;
         p.fault = nullptr;
+        p.wait_cycles = 0;
+        p.withhold_tile = -1;
         const int kind = d.kind;
         const int64_t base = (t - d.tile0) * TILE + (int64_t)threadIdx.x * WPT;
 #pragma unroll 1

@@ -44,6 +44,9 @@ struct BinopArgs {
     uint32_t negb;       /* ~0 flips b's sign slice (sub), 0 otherwise */
     int* fault;          /* device word set to 1 if a streamed kernel's wait
                             ran out of time; unused by the other kernels */
+    long long wait_cycles;   /* bound of each streamed-kernel wait (SM cycles) */
+    int64_t withhold_tile;   /* streamed kernel: tile whose copies are not issued
+                                (bsfp_stream_selftest); -1 otherwise */
 };
 
 template <int WPT> struct VecT;

@@ -28,6 +28,9 @@
  *
  * Waits are bounded (tma.cuh); a block whose wait gives up stops, lets its
  * copies in flight land, and sets *p.fault, which bsfp_fault_status reports.
+ * bsfp_stream_selftest exercises that path: it withholds the copies of one
+ * tile (p.withhold_tile) with a short bound, so the waits on that tile run
+ * out while every other wait completes.
  */
 #pragma once
 #include <cuda_runtime.h>
@@ -89,7 +92,9 @@ __global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_kernel(cons
             int64_t k = 0;   /* tiles issued by this block */
             for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
                 const int s = (int)(k % NST);
-                if (k >= NST && !mbar_wait(smem_addr(&empty[s]), (uint32_t)((k / NST - 1) & 1), ab)) break;
+                if (k >= NST && !mbar_wait(smem_addr(&empty[s]), (uint32_t)((k / NST - 1) & 1), ab, p.wait_cycles))
+                    break;
+                if (t == p.withhold_tile) continue;   /* self-test: nothing completes this stage */
                 const int64_t rem = p.S - t * TW;   /* > 0, a multiple of 32 */
                 const uint32_t bytes = (uint32_t)((rem < TW ? rem : TW) * 4);
                 const uint32_t bar = smem_addr(&full[s]);
@@ -104,7 +109,8 @@ __global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_kernel(cons
             /* the last phase issued on each stage has landed before the
              * block exits (at once, unless a wait gave up) */
             for (int64_t j = k > NST ? k - NST : 0; j < k; ++j)
-                mbar_drain(smem_addr(&full[j % NST]), (uint32_t)((j / NST) & 1));
+                if ((int64_t)blockIdx.x + j * gridDim.x != p.withhold_tile)
+                    mbar_drain(smem_addr(&full[j % NST]), (uint32_t)((j / NST) & 1), p.wait_cycles);
             if (*ab && p.fault) atomicExch(p.fault, 1);
         }
         return;
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_kernel(cons
     int64_t k = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int s = (int)(k % NST);
-        const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)((k / NST) & 1), ab);
+        const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)((k / NST) & 1), ab, p.wait_cycles);
         if (!__all_sync(0xFFFFFFFFu, ok)) break;   /* the warp leaves together */
         const uint32_t* src = ring + (size_t)s * NIN * TW + j0;
         uint32_t xa[B][WPT], xb[B][WPT], xc[1][WPT];

@@ -3,12 +3,13 @@
  * mbarriers and TMA bulk copies (cp.async.bulk) from global into shared
  * memory, completed on an mbarrier through its transaction count.
  *
- * Every wait is bounded: mbar_wait gives up after STREAM_WAIT_CYCLES SM
- * clock cycles (about two seconds at 2 GHz), raises the block's abort flag
- * and returns false, so a pipeline that stops making progress ends with an
- * error status instead of hanging the GPU.  mbar_drain is the same bound
- * without the abort check, used before a block exits to let copies still in
- * flight land in its shared memory.
+ * Every wait is bounded: mbar_wait gives up after `limit` SM clock cycles
+ * (STREAM_WAIT_CYCLES, about two seconds at 2 GHz, unless a self-test asks
+ * for less), raises the block's abort flag and returns false, so a pipeline
+ * that stops making progress ends with an error status instead of hanging
+ * the GPU.  mbar_drain is the same bound without the abort check, used
+ * before a block exits to let copies still in flight land in its shared
+ * memory.
  */
 #pragma once
 #include <cuda_runtime.h>
@@ -43,11 +44,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > STREAM_WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
@@ -55,10 +56,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return true;
 }
 
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > STREAM_WAIT_CYCLES) return;
+        if (clock64() - t0 > limit) return;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {

@@ -184,3 +184,40 @@ def test_small_calls_fall_back_to_the_grid_stride_kernel():
     finally:
         bs.bsfp_set_stream_min_tiles(0)
         bs.bsfp_set_variant(f, "mul", 0, 0)
+
+
+def test_bounded_wait_runs_out_and_reports():
+    """The failure path of the streamed kernel's waits: the copies of one tile
+    are withheld and the waits are bounded at 2^22 cycles (about 2 ms), so
+    the waits on that tile run out.  The block stops, the fault word becomes
+    1, the device stays usable, and the next normal call is exact."""
+    E, M = 5, 7
+    B = 1 + E + M
+    f = bs.Format(E, M)
+    TW, NST = shape(E, M)
+    n = bs.bsfp_num_sms() * (NST + 2) * 32 * TW
+    a = torch.zeros(B * bs.bsfp_plane_stride(n), dtype=torch.int32, device="cuda")
+    b = torch.zeros_like(a)
+    out = torch.zeros_like(a)
+    assert bs.bsfp_fault_status(clear=True) == 0
+    tiles = (bs.bsfp_plane_stride(n) + TW - 1) // TW
+    with pytest.raises(bs.BsfpError):
+        bs.bsfp_stream_selftest(f, "mul", a, b, out, n, tiles, 1 << 22)    # tile out of range
+    with pytest.raises(bs.BsfpError):
+        bs.bsfp_stream_selftest(f, "fma2", a, b, out, n, 0, 1 << 22)       # no streamed fma2
+    bs.bsfp_stream_selftest(f, "mul", a, b, out, n, -1, 1 << 22)           # nothing withheld
+    assert bs.bsfp_fault_status() == 0
+    bs.bsfp_stream_selftest(f, "mul", a, b, out, n, tiles // 2, 1 << 22)
+    assert bs.bsfp_fault_status(clear=True) == 1
+    assert bs.bsfp_fault_status() == 0
+    # the context still computes: a normal streamed call, exact against the oracle
+    m = 3 * 32 * TW + 5
+    x = synth.fp_values(E, M, m, 91).astype(np.uint32)
+    y = synth.fp_values(E, M, m, 92).astype(np.uint32)
+    px, py = dev(oracle.pack(B, x)), dev(oracle.pack(B, y))
+    o = torch.full_like(px, -1)
+    bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED)
+    bs.bsfp_mul(f, px, py, o, m)
+    assert (o.cpu().numpy().view(np.uint32).reshape(B, -1) == oracle.pack(B, oracle.binop("mul", E, M, 0, x, y))).all()
+    assert bs.bsfp_fault_status() == 0
+    bs.bsfp_set_variant(f, "mul", 0, 0)
