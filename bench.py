@@ -60,6 +60,33 @@ NCU_TRAFFIC = {(5, 7, "mul", 8): (218.137344e6 + 67.117568e6) * 4,
                (5, 7, "add", 2): (218.121216e6 + 71.256576e6) * 4}
 
 
+class DeviceTimer:
+    """Device time of single calls (CUDA events on the launching stream).
+    Before each timed call a 256 MB buffer is written on the same stream: it
+    evicts the 129 MB L2, so no operand is served from the previous call's
+    cache, and it keeps the GPU busy while the host enqueues the first event
+    and the call, so the host's launch latency is not counted."""
+
+    def __init__(self, torch, stream, flush_bytes: int = 256 << 20):
+        self.torch, self.stream = torch, stream
+        self.buf = torch.empty(flush_bytes // 4, dtype=torch.int32, device="cuda")
+
+    def ms(self, fn, reps: int = 5) -> float:
+        torch = self.torch
+        fn()
+        ts = []
+        with torch.cuda.stream(self.stream):
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                self.buf.fill_(0)
+                e0.record(self.stream)
+                fn()
+                e1.record(self.stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+
 def apply_tuning() -> int:
     from paper_1602_04716_gb300 import tune
     return tune.apply()
@@ -520,10 +547,11 @@ def run_serving(bs, torch, args, rank):
 def run_conversions(bs, torch, n, hbm):
     """bsfp_from_float (binary32 -> planes, RN), bsfp_to_float (planes ->
     binary32), bsfp_pack and bsfp_unpack for the two formats of the workload
-    at n elements: CUDA-event time (median of 5 after a warm-up) and
+    at n elements: CUDA-event time (median of 5 after a warm-up, DeviceTimer) and
     algorithmic GB/s (4 or the container bytes, + B/8 bytes per element)
     against the measured copy bandwidth."""
     stream = torch.cuda.current_stream()
+    timer = DeviceTimer(torch, stream)
     src = torch.empty(n, dtype=torch.float32, device="cuda")
     bs.bsfp_synth_fp_values(bs.Format(8, 23, 0), n, 2024, 0, 0, src)
     back = torch.empty(n, dtype=torch.float32, device="cuda")
@@ -538,16 +566,7 @@ def run_conversions(bs, torch, n, hbm):
                 ("to_float", lambda: bs.bsfp_to_float(f, planes, n, back, stream=stream), 4),
                 ("pack", lambda: bs.bsfp_pack(f, std, n, planes, stream=stream), cb),
                 ("unpack", lambda: bs.bsfp_unpack(f, planes, n, std, stream=stream), cb)):
-            fn()
-            ts = []
-            for _ in range(5):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1) * 1e-3)
-            t = float(np.median(ts))
+            t = timer.ms(fn) * 1e-3
             gbs = n * (bpe + (1 + E + M) / 8) / t / 1e9
             out["%s 1/%d/%d" % (name, E, M)] = {"ms": t * 1e3, "elements_per_s": n / t, "hbm_gbs": gbs,
                                                 "hbm_frac": gbs / hbm}
@@ -560,9 +579,10 @@ def run_conversions(bs, torch, n, hbm):
 def run_integers(bs, torch, n, hbm, L):
     """Integer bitslice vectors (Sec. 3) at the widths the paper names (5, 9,
     13 and 17 bits): add and mul modulo 2^w on n-element vectors of uniform
-    w-bit values; CUDA-event time (median of 5), GB/s of the algorithmic
+    w-bit values; CUDA-event time (median of 5, DeviceTimer), GB/s of the algorithmic
     bytes (3w/8 per element) and the roofline fraction."""
     stream = torch.cuda.current_stream()
+    timer = DeviceTimer(torch, stream)
     out = {}
     for w in (5, 9, 13, 17):
         # uniform random plane words are uniform random w-bit elements
@@ -572,17 +592,7 @@ def run_integers(bs, torch, n, hbm, L):
                 for _ in range(2)]
         res = torch.empty(words, dtype=torch.int32, device="cuda")
         for op in ("add", "mul"):
-            fn = lambda: bs.bsfp_int_op(op, w, ops_[0], ops_[1], res, n, stream=stream)
-            fn()
-            ts = []
-            for _ in range(5):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1) * 1e-3)
-            t = float(np.median(ts))
+            t = timer.ms(lambda: bs.bsfp_int_op(op, w, ops_[0], ops_[1], res, n, stream=stream)) * 1e-3
             G = bs.bsfp_int_gate_count(w, op)
             bpe = 3 * w / 8
             roof = min(hbm * 1e9 / bpe, L * 32 / G)
@@ -603,6 +613,7 @@ def run_small_case(bs, torch, rank):
     i = np.arange(n, dtype=np.uint32)
     out = {}
     stream = torch.cuda.current_stream()
+    timer = DeviceTimer(torch, stream)
     for rnd in (0, 1):
         f = bs.Format(4, 3, rnd)
         std = [torch.from_numpy(x.astype(np.uint8)).cuda() for x in (i >> 8, i & 255)]
@@ -610,17 +621,7 @@ def run_small_case(bs, torch, rank):
         back = bs.empty_standard(f, n)
 
         def timed(fn):
-            fn()
-            torch.cuda.synchronize()
-            ts = []
-            for _ in range(20):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1) * 1e3)
-            return float(np.median(ts))
+            return timer.ms(fn, reps=20) * 1e3
 
         r = "RZ" if rnd else "RN"
         out["pack_us"] = timed(lambda: bs.bsfp_pack(f, std[0], n, planes[0], stream=stream))
@@ -630,7 +631,8 @@ def run_small_case(bs, torch, rank):
                                                                  stream=stream))
         out["unpack_us"] = timed(lambda: bs.bsfp_unpack(f, planes[0], n, back, stream=stream))
         assert torch.equal(back, std[0])
-    out["workload"] = "1/4/3, all 65,536 operand pairs, single launches (median of 20, CUDA events)"
+    out["workload"] = ("1/4/3, all 65,536 operand pairs, single launches (median of 20, CUDA events around the "
+                       "kernel alone: L2 flushed and host launch latency excluded)")
     return out
 
 
@@ -638,13 +640,15 @@ def run_sweep(bs, torch, args, rank, hbm, L):
     """Format sweep: every 1/E/M with E in 3..8 and M in 2..23, n elements,
     bs_add, bs_mul, fma2 and bs_div under RN and RZ (and both with flush to zero for
     the formats compiled with it), operands from the same value
-    recipe.  Per launch: CUDA-event time (median of 3 after one warm-up), HBM
+    recipe.  Per launch: CUDA-event time (median of 3 after one warm-up, L2
+    flushed before each, host launch latency excluded: DeviceTimer), HBM
     GB/s of the algorithmic bytes, logic-op rate from the gate count, and the
     fraction of the roofline min(HBM peak / bytes per element, 32 * L / G).
     The RZ/RN ratios of time and gate count per op are the paper's one
     surviving quantitative claim (Sec. 5.2: RZ is markedly cheaper)."""
     n = args.sweep_n
     stream = torch.cuda.current_stream()
+    timer = DeviceTimer(torch, stream)
     rows = []
     for E in range(3, 9):
         for M in range(2, 24):
@@ -662,16 +666,8 @@ def run_sweep(bs, torch, args, rank, hbm, L):
             for rnd in modes:
                 f = bs.Format(E, M, rnd)
                 for op in SWEEP_OPS:
-                    ts = []
-                    for k in range(4):
-                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        e0.record(stream)
-                        bs.bsfp_op(op, f, ops_[0], ops_[1], out, n, c=ops_[2], stream=stream)
-                        e1.record(stream)
-                        e1.synchronize()
-                        if k:
-                            ts.append(e0.elapsed_time(e1) * 1e-3)
-                    t = float(np.median(ts))
+                    t = timer.ms(lambda: bs.bsfp_op(op, f, ops_[0], ops_[1], out, n, c=ops_[2], stream=stream),
+                                 reps=3) * 1e-3
                     nin = 3 if op == "fma2" else 2
                     bpe = (nin + 1) * B / 8
                     G = bs.bsfp_gate_count(f, op)

@@ -140,16 +140,16 @@ def main(argv=None):
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     for E, M in TUNED_FORMATS:
-        for rnd in (0, 1):
+        for rnd in (_b.RN, _b.RZ, _b.RN_FTZ, _b.RZ_FTZ):
             f = _b.Format(E, M, rnd)
             # the circuits have no data-dependent branches: operand values do not change the timing
             a, b, c = (torch.zeros(f.bits * _b.bsfp_plane_stride(args.n), dtype=torch.int32, device="cuda")
                        for _ in range(3))
             o = _b.empty_bitslice(f, args.n)
-            for op in ("add", "mul", "fma2"):
+            for op in ("add", "mul", "fma2", "div"):
                 best, table = autotune(op, f, a, b, c, o, args.n, path=args.out)
-                print("1/%d/%d %s %s: wpt %d, blocks/SM %d (%.3f ms)" % (E, M, "RZ" if rnd else "RN", op, best[0],
-                                                                        best[1], table[best]), flush=True)
+                print("1/%d/%d %s %s: wpt %d, blocks/SM %d (%.3f ms)" % (E, M, ("RN", "RZ", "RN_FTZ", "RZ_FTZ")[rnd],
+                                                                        op, best[0], best[1], table[best]), flush=True)
             del a, b, c, o
             torch.cuda.empty_cache()
     # the batched kernels on a mixed workload of the five batched formats
