@@ -186,7 +186,10 @@ typedef struct bsfp_batch_plan_st* bsfp_batch_plan;
 
 typedef enum {
     BSFP_BATCH_PERSISTENT = 0, /* one persistent kernel per op class over all tiles */
-    BSFP_BATCH_PLAIN = 1       /* one plain kernel launch per job, captured in the graph */
+    BSFP_BATCH_PLAIN = 1,      /* one plain kernel launch per job, captured in the graph */
+    BSFP_BATCH_STREAMED = 2    /* one streamed kernel (BSFP_VARIANT_STREAMED, in its job-list
+                                  form) per format, rounding and op class that has one, over the
+                                  tiles of all its jobs; the remaining jobs as in PERSISTENT */
 } bsfp_batch_mode;
 
 /* Launch shape of a plan.  wpt: words per thread in the persistent kernels
@@ -200,10 +203,13 @@ typedef struct {
 
 /* Build a plan for njobs independent jobs (not part of the paper: a batched
  * form of the Sec. 4 operations for many vectors of mixed formats).  Jobs
- * whose format is 1/4/3, 1/4/4, 1/5/7, 1/5/10 or 1/8/7 go to the persistent
- * kernels (one per op class: add/sub, mul, fma2; tiles handed out by an
- * atomic counter); any other compiled format runs as its plain kernel in the
- * same graph.  The plan owns a device buffer (job descriptors, the tile-to-
+ * whose format is 1/4/3, 1/4/4, 1/5/7, 1/5/10 or 1/8/7 (RN or RZ) go to the
+ * persistent kernels (one per op class: add/sub, mul, fma2; tiles handed
+ * out by an atomic counter); any other compiled format runs as its plain
+ * kernel in the same graph.  In BSFP_BATCH_STREAMED mode the add/sub and mul
+ * jobs of those formats, in every rounding mode, go instead to one streamed
+ * kernel per (format, rounding, op class), whose blocks take the tiles of
+ * all its jobs round-robin.  The plan owns a device buffer (job descriptors, the tile-to-
  * job map and the counters, allocated here) and a CUDA graph capturing
  * counter reset + kernels; it keeps the job pointers, which must stay valid
  * while the plan is run.  opt may be NULL.  Validation errors (any job)

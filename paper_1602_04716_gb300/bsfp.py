@@ -82,7 +82,7 @@ class bsfp_server_stats(ctypes.Structure):
         "arena_bytes_in_use", "arena_peak_bytes", "budget_bytes", "launches")]
 
 
-BATCH_PERSISTENT, BATCH_PLAIN = 0, 1
+BATCH_PERSISTENT, BATCH_PLAIN, BATCH_STREAMED = 0, 1, 2
 BATCH_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
 
 _lock = threading.Lock()

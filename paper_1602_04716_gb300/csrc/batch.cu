@@ -11,6 +11,7 @@
 #include "batch.cuh"
 #include "bsfp.h"
 #include "internal.h"
+#include "stream.cuh"
 
 namespace bsfp {
 
@@ -72,20 +73,57 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     bsfp_batch_options o = {BSFP_BATCH_PERSISTENT, 2, 0};
     if (opt) o = *opt;
     if (o.wpt == 0) o.wpt = 2;
-    if ((o.mode != BSFP_BATCH_PERSISTENT && o.mode != BSFP_BATCH_PLAIN) || (o.wpt != 1 && o.wpt != 2) ||
-        o.blocks_per_sm < 0 || o.blocks_per_sm > 64)
+    if ((o.mode != BSFP_BATCH_PERSISTENT && o.mode != BSFP_BATCH_PLAIN && o.mode != BSFP_BATCH_STREAMED) ||
+        (o.wpt != 1 && o.wpt != 2) || o.blocks_per_sm < 0 || o.blocks_per_sm > 64)
         return BSFP_ERR_SIZE;
 
-    /* validate every job and sort it into a persistent group or the plain list */
+    /* validate every job and sort it into a streamed group (BSFP_BATCH_STREAMED:
+     * one per format, rounding and op class with a streamed kernel), a
+     * persistent group (one per op class) or the plain list */
     std::vector<PreparedOp> prep((size_t)njobs);
     std::vector<int> group((size_t)njobs, -1);
+    struct SGroup {
+        const BinopEntry* e;
+        int* fault;
+        std::vector<StreamJob> jobs;
+        std::vector<int32_t> tmap;
+    };
+    std::vector<SGroup> sgroups;
     for (int32_t i = 0; i < njobs; ++i) {
         const bsfp_job& j = jobs[i];
-        const bsfp_status st = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &prep[(size_t)i]);
+        PreparedOp& po = prep[(size_t)i];
+        const bsfp_status st = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &po);
         if (st != BSFP_OK) return st;
-        if (o.mode == BSFP_BATCH_PERSISTENT && !prep[(size_t)i].skip && prep[(size_t)i].opc < OPC_COUNT &&
-            batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0)
-            group[(size_t)i] = prep[(size_t)i].opc;
+        if (po.skip) continue;
+        if (o.mode == BSFP_BATCH_STREAMED && (po.opc == OPC_ADDSUB || po.opc == OPC_MUL) &&
+            (po.entry->wpt_mask & (unsigned)VARIANT_STREAMED) && po.entry->stream_batch_launch) {
+            size_t gi = 0;
+            while (gi < sgroups.size() && sgroups[gi].e != po.entry) ++gi;
+            if (gi == sgroups.size()) sgroups.push_back(SGroup{po.entry, po.args.fault, {}, {}});
+            SGroup& g = sgroups[gi];
+            const BinopArgs& a = po.args;
+            StreamJob sj;
+            sj.a = a.a;
+            sj.b = a.b;
+            sj.out = a.out;
+            sj.S = a.S;
+            sj.nwords = a.nwords;
+            sj.tile0 = (int64_t)g.tmap.size();
+            sj.tailmask = a.tailmask;
+            sj.negb = a.negb;
+            const int64_t nt = (a.S + po.entry->stream_tw - 1) / po.entry->stream_tw;
+            const int32_t idx = (int32_t)g.jobs.size();
+            g.jobs.push_back(sj);
+            for (int64_t t = 0; t < nt; ++t) g.tmap.push_back(idx);
+            group[(size_t)i] = OPC_COUNT;   /* handled by a streamed group */
+            continue;
+        }
+        if (o.mode != BSFP_BATCH_PLAIN && po.opc < OPC_COUNT && batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0)
+            group[(size_t)i] = po.opc;
+    }
+    for (SGroup& g : sgroups) {
+        const cudaError_t e = g.e->stream_batch_prepare();
+        if (e != cudaSuccess) return set_cuda_error(e);
     }
 
     /* tiles per group */
@@ -94,7 +132,7 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     std::vector<int32_t> tmap[OPC_COUNT];
     for (int32_t i = 0; i < njobs; ++i) {
         const int g = group[(size_t)i];
-        if (g < 0) continue;
+        if (g < 0 || g >= OPC_COUNT) continue;
         const bsfp_job& j = jobs[i];
         const BinopArgs& a = prep[(size_t)i].args;
         JobDesc d;
@@ -115,7 +153,8 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         for (int64_t t = 0; t < nt; ++t) tmap[g].push_back(idx);
     }
 
-    /* one device buffer: descriptors, tile maps, counters */
+    /* one device buffer: descriptors, tile maps, counters; then the streamed
+     * groups' job lists and tile maps */
     size_t off_desc[OPC_COUNT], off_map[OPC_COUNT], off_cnt[OPC_COUNT], total = 0;
     for (int g = 0; g < OPC_COUNT; ++g) {
         off_desc[g] = total;
@@ -124,6 +163,13 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         total = align_up(total + tmap[g].size() * sizeof(int32_t), 256);
         off_cnt[g] = total;
         total = align_up(total + sizeof(unsigned long long), 256);
+    }
+    std::vector<size_t> off_sjobs(sgroups.size()), off_smap(sgroups.size());
+    for (size_t g = 0; g < sgroups.size(); ++g) {
+        off_sjobs[g] = total;
+        total = align_up(total + sgroups[g].jobs.size() * sizeof(StreamJob), 256);
+        off_smap[g] = total;
+        total = align_up(total + sgroups[g].tmap.size() * sizeof(int32_t), 256);
     }
 
     bsfp_batch_plan p = new bsfp_batch_plan_st();
@@ -138,6 +184,13 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
                                                cudaMemcpyHostToDevice);
         if (err == cudaSuccess && !tmap[g].empty())
             err = cudaMemcpy(base + off_map[g], tmap[g].data(), tmap[g].size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice);
+    }
+    for (size_t g = 0; g < sgroups.size() && err == cudaSuccess; ++g) {
+        err = cudaMemcpy(base + off_sjobs[g], sgroups[g].jobs.data(), sgroups[g].jobs.size() * sizeof(StreamJob),
+                         cudaMemcpyHostToDevice);
+        if (err == cudaSuccess)
+            err = cudaMemcpy(base + off_smap[g], sgroups[g].tmap.data(), sgroups[g].tmap.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice);
     }
     if (err != cudaSuccess) {
@@ -173,6 +226,17 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     bsfp_status st = BSFP_OK;
     err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
+        /* streamed groups: one block per SM, at most one per tile */
+        for (size_t g = 0; g < sgroups.size() && st == BSFP_OK; ++g) {
+            const int64_t ntiles = (int64_t)sgroups[g].tmap.size();
+            const int64_t sms = device_num_sms();
+            const cudaError_t e2 = sgroups[g].e->stream_batch_launch(
+                reinterpret_cast<const StreamJob*>(base + off_sjobs[g]),
+                reinterpret_cast<const int32_t*>(base + off_smap[g]), ntiles, sgroups[g].fault,
+                (int)(ntiles < sms ? ntiles : sms), cs);
+            if (e2 != cudaSuccess) st = set_cuda_error(e2);
+            else p->launches += 1;
+        }
         for (int g = 0; g < OPC_COUNT && st == BSFP_OK; ++g) {
             if (tmap[g].empty()) continue;
             unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + off_cnt[g]);

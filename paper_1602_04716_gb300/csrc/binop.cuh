@@ -183,6 +183,9 @@ typedef cudaError_t (*binop_launch_fn)(const BinopArgs& p, int wpt, int grid, cu
 typedef const void* (*binop_kernel_fn)(int wpt);
 typedef cudaError_t (*stream_launch_fn)(const BinopArgs& p, int grid, cudaStream_t s);
 typedef cudaError_t (*stream_prepare_fn)();
+struct StreamJob;
+typedef cudaError_t (*stream_batch_launch_fn)(const StreamJob* jobs, const int32_t* tile_job, int64_t ntiles,
+                                              int* fault, int grid, cudaStream_t s);
 
 /* Variant code of the streamed kernel (stream.cuh) beside the words-per-
  * thread codes 1, 2 and 4 of the grid-stride kernel. */
@@ -198,6 +201,9 @@ struct BinopEntry {
     stream_launch_fn stream_launch = nullptr;
     stream_prepare_fn stream_prepare = nullptr;   /* opts in to its shared memory */
     int stream_tw = 0;                            /* words per plane per tile */
+    /* its job-list form, for the batched plans */
+    stream_batch_launch_fn stream_batch_launch = nullptr;
+    stream_prepare_fn stream_batch_prepare = nullptr;
 };
 
 template <int E, int M, int R, int OPC>

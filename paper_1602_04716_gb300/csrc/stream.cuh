@@ -143,6 +143,154 @@ __global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_kernel(cons
     if (lane == 0 && *ab && p.fault) atomicExch(p.fault, 1);
 }
 
+/* ------------------------------------------------------------ job lists ---
+ * stream_batch_kernel: the same pipeline over the tiles of many vectors of
+ * one (format, rounding, op class), for the batched plans (bsfp.h,
+ * BSFP_BATCH_STREAMED).  Each vector is cut into tiles of TW word columns;
+ * tile_job[t] names the vector of tile t, and tiles go to blocks
+ * round-robin.  The producer reads the tile's descriptor (prefetched one
+ * tile ahead), writes what the consumers need -- output, stride, tail mask,
+ * sign flip, first column -- into the stage's metadata slot, then arrives
+ * with the stage's byte count and issues the copies; the consumers take the
+ * metadata into registers before they release the stage. */
+struct StreamJob {
+    const uint32_t* a;
+    const uint32_t* b;
+    uint32_t* out;
+    int64_t S;
+    int64_t nwords;
+    int64_t tile0;      /* first tile of this vector in the plan's tile list */
+    uint32_t tailmask;
+    uint32_t negb;
+};
+
+struct StreamTileMeta {
+    uint32_t* out;
+    int64_t S;
+    int64_t nwords;
+    int64_t w0;         /* first word column of the tile */
+    uint32_t tailmask;
+    uint32_t negb;
+};
+
+template <int E, int M>
+struct StreamBatchShape {
+    using SH = StreamShape<E, M>;
+    static constexpr int HDR = 256;   /* barriers, then one metadata slot per stage */
+    static constexpr int META_OFF = 64;
+    static constexpr size_t SMEM = HDR + (size_t)SH::NST * SH::NIN * SH::TW * 4;
+    static_assert(2 * SH::NST * 8 <= META_OFF, "barriers fit before the metadata");
+    static_assert(META_OFF + SH::NST * sizeof(StreamTileMeta) <= HDR, "metadata fits the header");
+    static_assert(SMEM <= 232448, "ring fits the shared memory one block may opt in to");
+};
+
+template <int E, int M, int R, int OPC>
+__global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_batch_kernel(
+    const StreamJob* __restrict__ jobs, const int32_t* __restrict__ tile_job, int64_t ntiles, int* fault) {
+    using SH = StreamShape<E, M>;
+    using SB = StreamBatchShape<E, M>;
+    constexpr int B = SH::B, NC = SH::NC, NST = SH::NST, NIN = SH::NIN, TW = SH::TW, WPT = SH::WPT;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + NST;
+    StreamTileMeta* meta = reinterpret_cast<StreamTileMeta*>(smem + SB::META_OFF);
+    uint32_t* ring = reinterpret_cast<uint32_t*>(smem + SB::HDR);
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(smem_addr(&full[s]), 1);
+            mbar_init(smem_addr(&empty[s]), NC);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    volatile int* ab = &abort_flag;
+
+    if (warp == NC) {
+        if (lane == 0) {
+            int64_t k = 0;
+            StreamJob nj;
+            if ((int64_t)blockIdx.x < ntiles) nj = jobs[tile_job[blockIdx.x]];
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+                const StreamJob J = nj;
+                const int64_t tn = t + gridDim.x;
+                if (tn < ntiles) nj = jobs[tile_job[tn]];   /* next descriptor, in flight meanwhile */
+                const int s = (int)(k % NST);
+                if (k >= NST && !mbar_wait(smem_addr(&empty[s]), (uint32_t)((k / NST - 1) & 1), ab, STREAM_WAIT_CYCLES))
+                    break;
+                const int64_t w0 = (t - J.tile0) * TW;
+                const int64_t rem = J.S - w0;   /* > 0, a multiple of 32 */
+                const uint32_t bytes = (uint32_t)((rem < TW ? rem : TW) * 4);
+                StreamTileMeta& m = meta[s];
+                m.out = J.out;
+                m.S = J.S;
+                m.nwords = J.nwords;
+                m.w0 = w0;
+                m.tailmask = J.tailmask;
+                m.negb = J.negb;
+                const uint32_t bar = smem_addr(&full[s]);
+                mbar_arrive_expect_tx(bar, bytes * NIN);   /* release: the metadata is visible with the phase */
+                const uint32_t dst = smem_addr(ring + (size_t)s * NIN * TW);
+#pragma unroll 1
+                for (int q = 0; q < NIN; ++q) {
+                    const uint32_t* src = (q < B) ? J.a + (int64_t)q * J.S : J.b + (int64_t)(q - B) * J.S;
+                    bulk_copy_g2s(dst + (uint32_t)(q * TW * 4), src + w0, bytes, bar);
+                }
+            }
+            for (int64_t j = k > NST ? k - NST : 0; j < k; ++j)
+                mbar_drain(smem_addr(&full[j % NST]), (uint32_t)((j / NST) & 1), STREAM_WAIT_CYCLES);
+            if (*ab && fault) atomicExch(fault, 1);
+        }
+        return;
+    }
+
+    const int j0 = (warp * 32 + lane) * WPT;
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = (int)(k % NST);
+        const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)((k / NST) & 1), ab, STREAM_WAIT_CYCLES);
+        if (!__all_sync(0xFFFFFFFFu, ok)) break;
+        BinopArgs p;
+        p.out = meta[s].out;
+        p.S = meta[s].S;
+        p.nwords = meta[s].nwords;
+        p.tailmask = meta[s].tailmask;
+        p.negb = meta[s].negb;
+        const int64_t w0 = meta[s].w0 + j0;
+        const uint32_t* src = ring + (size_t)s * NIN * TW + j0;
+        uint32_t xa[B][WPT], xb[B][WPT], xc[1][WPT];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+#pragma unroll
+            for (int w = 0; w < WPT; ++w) {
+                xa[i][w] = src[i * TW + w];
+                xb[i][w] = src[(B + i) * TW + w];
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
+        /* the tile may be the shorter last one of its vector */
+        if (w0 < p.S) binop_compute_store<E, M, R, OPC, WPT>(p, w0, xa, xb, xc);
+    }
+    if (lane == 0 && *ab && fault) atomicExch(fault, 1);
+}
+
+template <int E, int M, int R, int OPC>
+cudaError_t stream_batch_launch(const StreamJob* jobs, const int32_t* tile_job, int64_t ntiles, int* fault, int grid,
+                                cudaStream_t s) {
+    stream_batch_kernel<E, M, R, OPC>
+        <<<grid, StreamShape<E, M>::THREADS, StreamBatchShape<E, M>::SMEM, s>>>(jobs, tile_job, ntiles, fault);
+    return cudaGetLastError();
+}
+
+template <int E, int M, int R, int OPC>
+cudaError_t stream_batch_prepare() {
+    return cudaFuncSetAttribute(stream_batch_kernel<E, M, R, OPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)StreamBatchShape<E, M>::SMEM);
+}
+
 template <int E, int M, int R, int OPC>
 cudaError_t stream_launch(const BinopArgs& p, int grid, cudaStream_t s) {
     using SH = StreamShape<E, M>;

@@ -88,6 +88,47 @@ def test_persistent_plan_small_grids(blocks_per_sm):
     plan.free()
 
 
+def test_streamed_plan_matches_oracle_and_replays():
+    """BSFP_BATCH_STREAMED: add/sub/mul jobs of the five batched formats (all
+    four rounding modes) run as one streamed kernel per (format, rounding, op
+    class) over the tiles of all its jobs, fma2 as the persistent kernels,
+    everything else as plain launches; every job exact, and again on a
+    replay of the graph."""
+    jobs = _make_batch(220, 5100)
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    groups = {(j["E"], j["M"], j["rnd"], j["op"] == "mul") for j in jobs
+              if (j["E"], j["M"]) in bs.BATCH_FORMATS and j["op"] in ("add", "sub", "mul") and j["n"] > 0}
+    n_plain = sum(1 for j in jobs if j["n"] > 0 and ((j["E"], j["M"]) not in bs.BATCH_FORMATS or j["op"] == "div" or
+                                                     (j["op"] == "fma2" and j["rnd"] > 1)))
+    n_persistent = 1 if any(j["op"] == "fma2" and j["rnd"] < 2 and (j["E"], j["M"]) in bs.BATCH_FORMATS and j["n"] > 0
+                            for j in jobs) else 0
+    assert plan.launches == len(groups) + n_persistent + n_plain
+    for _ in range(2):
+        _clear(jobs)
+        plan.run()
+        torch.cuda.synchronize()
+        _check_all(jobs)
+    assert bs.bsfp_fault_status() == 0
+    plan.free()
+
+
+def test_streamed_plan_many_tiles_per_block():
+    """Jobs up to 2^20 elements of the batched formats only: each streamed
+    group has more tiles than SMs, so every block goes round its ring."""
+    jobs = _make_batch(48, 7300, max_len=1 << 20, extra_formats=())
+    for j in jobs:
+        if j["op"] in ("fma2", "div"):
+            j["op"] = "mul"
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    plan.run()
+    torch.cuda.synchronize()
+    _check_all(jobs)
+    assert bs.bsfp_fault_status() == 0
+    plan.free()
+
+
 def test_plain_graph_and_plain_launches_match():
     jobs = _make_batch(120, 8000)
     arr, nj = _ctypes_jobs(jobs)
