@@ -416,14 +416,17 @@ int32_t bsfp_variants_compiled(bsfp_format f, int32_t op);
 /* Override the launch shape for (format, op): wpt in {1, 2, 4,
  * BSFP_VARIANT_STREAMED} (must be compiled; 0 restores the default) and
  * blocks_per_sm (0 = occupancy maximum, larger values are capped at it;
- * ignored by the streamed kernel, which runs one block per SM).  sub shares
- * add's shape.  Used by the autotuner; returns BSFP_ERR_UNSUPPORTED for an
- * uncompiled variant.  Not synchronised with launches already queued: it
- * affects later calls. */
+ * ignored by the streamed kernel, which runs one block per SM).  A
+ * grid-stride shape (or 0) also becomes the fallback that the streamed
+ * variant gives way to for calls too small for it (bsfp_set_stream_min_tiles);
+ * setting BSFP_VARIANT_STREAMED keeps the fallback.  sub shares add's shape.
+ * Used by the autotuner; returns BSFP_ERR_UNSUPPORTED for an uncompiled
+ * variant.  Not synchronised with launches already queued: it affects later
+ * calls. */
 bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blocks_per_sm);
 /* The variant a call of (format, op) on n elements launches: the one
  * bsfp_variant reports, except that the streamed variant gives way to the
- * default grid-stride variant when the call has fewer than
+ * fallback grid-stride shape (bsfp_set_variant) when the call has fewer than
  * tiles_per_sm x SMs tiles of the streamed kernel (its ring would never
  * fill).  -1 on a bad argument, 0 if the format is not compiled.  Needs the
  * device only for its SM count. */

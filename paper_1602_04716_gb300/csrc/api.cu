@@ -106,7 +106,15 @@ static int* fault_word(int dev) {
 struct Shape {
     int8_t wpt;
     int16_t bps;
+    /* the grid-stride shape the streamed variant gives way to for calls too
+     * small for it: the last grid-stride shape set (0 = the default) */
+    int8_t fb_wpt;
+    int16_t fb_bps;
 };
+
+/* Variant and blocks/SM of a call on S plane words under shape sh (the
+ * lock on the shapes held). */
+static void pick_shape(const Shape& sh, const BinopEntry* e, int64_t S, int* wpt, int* bps);
 static Shape g_shape[TAB_E][TAB_M][TAB_R][OPC_ALL];
 static int g_occ[TAB_E][TAB_M][TAB_R][OPC_ALL][5];   /* cached occupancy per wpt */
 static std::mutex g_shape_mu;
@@ -199,18 +207,10 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
     int wpt, bps;
     {
         std::lock_guard<std::mutex> lk(g_shape_mu);
-        const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
-        wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
-        if (wpt == VARIANT_STREAMED) {
-            const int64_t tiles = (p.S + e->stream_tw - 1) / e->stream_tw;
-            if (tiles < (int64_t)g_stream_min_tiles.load(std::memory_order_relaxed) * device_num_sms())
-                wpt = e->default_wpt;
-        }
-        if (wpt == VARIANT_STREAMED) {
-            bps = 1;
-        } else {
+        pick_shape(g_shape[f.exp_bits][f.man_bits][f.rnd][opc], e, p.S, &wpt, &bps);
+        if (wpt != VARIANT_STREAMED) {
             const int occ = occupancy(f, opc, e, wpt);
-            bps = (sh.bps > 0 && sh.bps < occ) ? sh.bps : occ;
+            bps = (bps > 0 && bps < occ) ? bps : occ;
         }
     }
     if (wpt == VARIANT_STREAMED) {
@@ -235,6 +235,22 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
     po->wpt = wpt;
     po->grid = (int)(need < cap ? need : cap);
     return BSFP_OK;
+}
+
+static void pick_shape(const Shape& sh, const BinopEntry* e, int64_t S, int* wpt, int* bps) {
+    *wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
+    *bps = sh.bps;
+    if (*wpt == VARIANT_STREAMED) {
+        const int64_t tiles = (S + e->stream_tw - 1) / e->stream_tw;
+        if (tiles >= (int64_t)g_stream_min_tiles.load(std::memory_order_relaxed) * device_num_sms()) {
+            *bps = 1;
+            return;
+        }
+        /* too small to fill the ring: the fallback grid-stride shape */
+        const bool fb = sh.fb_wpt && (e->wpt_mask & (unsigned)sh.fb_wpt);
+        *wpt = fb ? sh.fb_wpt : e->default_wpt;
+        *bps = fb ? sh.fb_bps : 0;
+    }
 }
 
 bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s) {
@@ -513,7 +529,10 @@ bsfp_status bsfp_stream_selftest(bsfp_format f, int32_t op, const uint32_t* a, c
     {
         std::lock_guard<std::mutex> lk(g_shape_mu);
         saved = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
-        g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = Shape{(int8_t)VARIANT_STREAMED, 0};
+        Shape forced = saved;
+        forced.wpt = (int8_t)VARIANT_STREAMED;
+        forced.bps = 0;
+        g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = forced;
     }
     min_tiles = g_stream_min_tiles.exchange(0);
     PreparedOp po;
@@ -544,18 +563,9 @@ int32_t bsfp_variant_for(bsfp_format f, int32_t op, int64_t n) {
     const int opc = opclass(op);
     const BinopEntry* e = entry_for(f, opc);
     if (!e) return 0;
-    int wpt;
-    {
-        std::lock_guard<std::mutex> lk(g_shape_mu);
-        const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
-        wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
-    }
-    if (wpt == VARIANT_STREAMED) {
-        const int64_t S = bsfp_plane_stride(n);
-        const int64_t tiles = (S + e->stream_tw - 1) / e->stream_tw;
-        if (tiles < (int64_t)g_stream_min_tiles.load(std::memory_order_relaxed) * device_num_sms())
-            wpt = e->default_wpt;
-    }
+    int wpt, bps;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    pick_shape(g_shape[f.exp_bits][f.man_bits][f.rnd][opc], e, bsfp_plane_stride(n), &wpt, &bps);
     return wpt;
 }
 
@@ -577,7 +587,13 @@ bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blo
     const BinopEntry* e = entry_for(f, opc);
     if (!e || (wpt != 0 && !(e->wpt_mask & (unsigned)wpt))) return BSFP_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_shape_mu);
-    g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = Shape{(int8_t)wpt, (int16_t)blocks_per_sm};
+    Shape& sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+    sh.wpt = (int8_t)wpt;
+    sh.bps = (int16_t)blocks_per_sm;
+    if (wpt != VARIANT_STREAMED) {   /* a grid-stride shape (or the default) is also the fallback */
+        sh.fb_wpt = (int8_t)wpt;
+        sh.fb_bps = (int16_t)blocks_per_sm;
+    }
     return BSFP_OK;
 }
 

@@ -101,6 +101,11 @@ bsfp_status bsfp_autotune(bsfp_format f, int32_t op, const char* cache_path) {
         bsfp_set_variant(f, op, 0, 0);
         return st;
     }
+    /* back to the default first, so that a streamed best keeps the default
+     * grid-stride shape as its fallback for calls too small for it (the
+     * shapes timed here are the fastest at 2^28 elements, not for small
+     * calls) */
+    bsfp_set_variant(f, op, 0, 0);
     st = bsfp_set_variant(f, op, best_wpt, best_bps);
     if (st != BSFP_OK || !cache_path) return st;
 

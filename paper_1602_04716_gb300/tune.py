@@ -50,6 +50,7 @@ def apply(path: str = CACHE) -> int:
         e, m, r, op = key.split("/")
         f = _b.Format(int(e), int(m), int(r))
         if v["wpt"] in _b.bsfp_variants_compiled(f, op):
+            _b.bsfp_set_variant(f, op, 0, 0)   # the default stays the streamed variant's fallback
             _b.bsfp_set_variant(f, op, v["wpt"], v["bps"])
             n += 1
     return n
@@ -81,6 +82,9 @@ def autotune(op, f, a, b, c, out, n, bps_choices=(0, 1, 2, 3, 4, 6, 8), reps=5, 
             _b.bsfp_set_variant(f, op, wpt, bps)
             table[(wpt, bps)] = time_op(op, f, a, b, c, out, n, reps)
     best = min(table, key=table.get)
+    # back to the default first: a streamed best then keeps the default grid-stride shape as its
+    # fallback for calls too small for it (the shapes timed here are the fastest at n elements only)
+    _b.bsfp_set_variant(f, op, 0, 0)
     _b.bsfp_set_variant(f, op, best[0], best[1])
     if path:
         cache = load(path)

@@ -94,9 +94,19 @@ def test_stream_threshold_and_variant_query_arguments():
     assert bs.bsfp_variant_for(bs.Format(9, 7), "mul", 10) == -1
     assert bs.bsfp_variant_for(bs.Format(5, 7), 9, 10) == -1
     assert bs.bsfp_variant_for(bs.Format(5, 7), "mul", -1) == -1
-    bs.bsfp_set_variant(bs.Format(5, 7), "mul", 2, 0)
-    assert bs.bsfp_variant_for(bs.Format(5, 7), "mul", 1 << 20) == 2
-    bs.bsfp_set_variant(bs.Format(5, 7), "mul", 0, 0)
+    f = bs.Format(5, 7)
+    bs.bsfp_set_variant(f, "mul", 2, 0)
+    assert bs.bsfp_variant_for(f, "mul", 1 << 20) == 2
+    # a grid-stride shape set before the streamed variant is its fallback for small calls
+    bs.bsfp_set_variant(f, "mul", 4, 3)
+    bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED)
+    assert bs.bsfp_variant(f, "mul") == bs.VARIANT_STREAMED
+    assert bs.bsfp_variant_for(f, "mul", 1) == 4
+    assert bs.bsfp_variant_for(f, "mul", 1 << 32) == bs.VARIANT_STREAMED
+    bs.bsfp_set_variant(f, "mul", 0, 0)   # back to the default, fallback included
+    bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED)
+    assert bs.bsfp_variant_for(f, "mul", 1) == bs.bsfp_variants_compiled(f, "mul")[1]   # default: 2 words/thread
+    bs.bsfp_set_variant(f, "mul", 0, 0)
 
 
 def test_variants_and_overrides():
