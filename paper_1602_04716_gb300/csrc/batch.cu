@@ -224,18 +224,44 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         return set_cuda_error(err);
     }
     bsfp_status st = BSFP_OK;
-    err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    /* side streams and events for the streamed groups' parallel branches */
+    constexpr int NBRANCH = 8;
+    const int nside = (int)(sgroups.size() < (size_t)NBRANCH ? sgroups.size() : (size_t)NBRANCH);
+    cudaStream_t side[NBRANCH] = {};
+    cudaEvent_t fork = nullptr, join[NBRANCH] = {};
+    for (int i = 0; i < nside && err == cudaSuccess; ++i) {
+        err = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    }
+    if (err == cudaSuccess && nside) err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
-        /* streamed groups: one block per SM, at most one per tile */
+        /* streamed groups: one block per SM, at most one per tile.  The
+         * groups are independent, so they are captured as parallel branches
+         * (group g on side stream g mod 8): one group's blocks take the SMs
+         * that another's last tiles leave idle, instead of each launch
+         * ramping up and draining on its own. */
+        if (nside) {
+            cudaError_t e2 = cudaEventRecord(fork, cs);
+            for (int i = 0; i < nside && e2 == cudaSuccess; ++i) e2 = cudaStreamWaitEvent(side[i], fork, 0);
+            if (e2 != cudaSuccess) st = set_cuda_error(e2);
+        }
         for (size_t g = 0; g < sgroups.size() && st == BSFP_OK; ++g) {
             const int64_t ntiles = (int64_t)sgroups[g].tmap.size();
             const int64_t sms = device_num_sms();
             const cudaError_t e2 = sgroups[g].e->stream_batch_launch(
                 reinterpret_cast<const StreamJob*>(base + off_sjobs[g]),
                 reinterpret_cast<const int32_t*>(base + off_smap[g]), ntiles, sgroups[g].fault,
-                (int)(ntiles < sms ? ntiles : sms), cs);
+                (int)(ntiles < sms ? ntiles : sms), side[g % NBRANCH]);
             if (e2 != cudaSuccess) st = set_cuda_error(e2);
             else p->launches += 1;
+        }
+        /* join every branch back (also after an error: the capture must end
+         * with all its streams joined) */
+        for (int i = 0; i < nside; ++i) {
+            cudaError_t e2 = cudaEventRecord(join[i], side[i]);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, join[i], 0);
+            if (e2 != cudaSuccess && st == BSFP_OK) st = set_cuda_error(e2);
         }
         for (int g = 0; g < OPC_COUNT && st == BSFP_OK; ++g) {
             if (tmap[g].empty()) continue;
@@ -260,6 +286,11 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     } else {
         st = set_cuda_error(err);
     }
+    for (int i = 0; i < nside; ++i) {
+        if (side[i]) cudaStreamDestroy(side[i]);
+        if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
     cudaStreamDestroy(cs);
     if (st == BSFP_OK) {
         err = cudaGraphInstantiate(&p->exec, p->graph, 0);
