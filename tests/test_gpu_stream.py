@@ -221,3 +221,26 @@ def test_bounded_wait_runs_out_and_reports():
     assert (o.cpu().numpy().view(np.uint32).reshape(B, -1) == oracle.pack(B, oracle.binop("mul", E, M, 0, x, y))).all()
     assert bs.bsfp_fault_status() == 0
     bs.bsfp_set_variant(f, "mul", 0, 0)
+
+
+@pytest.mark.parametrize("op", ["add", "mul"])
+def test_in_place_output(op):
+    """out may equal an input (the C ABI allows exact aliasing): the streamed
+    kernel reads a tile into shared memory before any of its columns is
+    written, so out = a gives the same result as a separate output."""
+    E, M = 5, 7
+    B = 1 + E + M
+    f = bs.Format(E, M)
+    TW, NST = shape(E, M)
+    n = bs.bsfp_num_sms() * (NST + 1) * 32 * TW + 999
+    a = synth.fp_values(E, M, n, 61).astype(np.uint32)
+    b = synth.fp_values(E, M, n, 62).astype(np.uint32)
+    pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+    bs.bsfp_set_variant(f, op, bs.VARIANT_STREAMED)
+    bs.bsfp_op(op, f, pa, pb, pa, n)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 20000), np.arange(n - 100, n)]))
+    got = oracle.unpack(B, pa.cpu().numpy().view(np.uint32), n)[idx]
+    assert (got == oracle.binop(op, E, M, 0, a[idx], b[idx])).all()
+    bs.bsfp_set_variant(f, op, 0, 0)
