@@ -249,3 +249,15 @@ def test_autotune_arguments_and_cache_loading(tmp_path):
     assert bs.bsfp_variant(bs.Format(4, 4, 1), "add") == 1
     bs.bsfp_set_variant(bs.Format(5, 7, 0), "mul", 0, 0)
     bs.bsfp_set_variant(bs.Format(4, 4, 1), "add", 0, 0)
+
+
+def test_batch_plan_options_validated_before_any_cuda_call():
+    """Plan modes are PERSISTENT (0), PLAIN (1) and STREAMED (2); anything
+    else, or a bad shape, is refused before a job is looked at."""
+    L = _binding._lib()
+    h = ctypes.c_void_p()
+    for mode, wpt, bps in ((3, 0, 0), (-1, 0, 0), (bs.BATCH_STREAMED, 3, 0), (bs.BATCH_STREAMED, 0, 65)):
+        opt = bs.bsfp_batch_options(mode, wpt, bps)
+        assert L.bsfp_batch_plan_create(None, 0, ctypes.byref(opt), ctypes.byref(h)) == bs.ERR_SIZE
+    assert L.bsfp_batch_plan_create(None, -1, None, ctypes.byref(h)) == bs.ERR_SIZE
+    assert L.bsfp_batch_plan_create(None, 1, None, ctypes.byref(h)) == bs.ERR_NULL
