@@ -170,9 +170,21 @@ static int occupancy(const bsfp_format& f, int opc, const BinopEntry* e, int wpt
 }
 
 /* Validate one element-wise op and work out its launch: kernel entry, args,
- * words per thread and grid.  Returns BSFP_OK with *skip set when n == 0. */
+ * words per thread and grid.  Returns BSFP_OK with *skip set when n == 0.
+ * force_streamed: take the streamed kernel whatever the shape table and the
+ * call's size (the caller has checked that it is compiled). */
+static bsfp_status prepare_binop_impl(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b,
+                                      const uint32_t* c, uint32_t* out, int64_t n, PreparedOp* po,
+                                      bool force_streamed);
+
 bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
                           uint32_t* out, int64_t n, PreparedOp* po) {
+    return prepare_binop_impl(f, op, a, b, c, out, n, po, false);
+}
+
+static bsfp_status prepare_binop_impl(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b,
+                                      const uint32_t* c, uint32_t* out, int64_t n, PreparedOp* po,
+                                      bool force_streamed) {
     po->skip = false;
     if (!format_ok(f)) return BSFP_ERR_FORMAT;
     const int opc = opclass(op);
@@ -205,7 +217,10 @@ bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const
     const int dev = current_device();
     p.fault = fault_word(dev);
     int wpt, bps;
-    {
+    if (force_streamed) {
+        wpt = VARIANT_STREAMED;
+        bps = 1;
+    } else {
         std::lock_guard<std::mutex> lk(g_shape_mu);
         pick_shape(g_shape[f.exp_bits][f.man_bits][f.rnd][opc], e, p.S, &wpt, &bps);
         if (wpt != VARIANT_STREAMED) {
@@ -523,25 +538,9 @@ bsfp_status bsfp_stream_selftest(bsfp_format f, int32_t op, const uint32_t* a, c
     if (n <= 0) return BSFP_ERR_SIZE;
     const BinopEntry* e = entry_for(f, opc);
     if (!e || !(e->wpt_mask & (unsigned)VARIANT_STREAMED)) return BSFP_ERR_UNSUPPORTED;
-    /* run the streamed kernel whatever the shape settings and size */
-    Shape saved;
-    int32_t min_tiles;
-    {
-        std::lock_guard<std::mutex> lk(g_shape_mu);
-        saved = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
-        Shape forced = saved;
-        forced.wpt = (int8_t)VARIANT_STREAMED;
-        forced.bps = 0;
-        g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = forced;
-    }
-    min_tiles = g_stream_min_tiles.exchange(0);
+    /* the streamed kernel whatever the shape settings and size */
     PreparedOp po;
-    bsfp_status st = prepare_binop(f, op, a, b, nullptr, out, n, &po);
-    g_stream_min_tiles.store(min_tiles);
-    {
-        std::lock_guard<std::mutex> lk(g_shape_mu);
-        g_shape[f.exp_bits][f.man_bits][f.rnd][opc] = saved;
-    }
+    bsfp_status st = prepare_binop_impl(f, op, a, b, nullptr, out, n, &po, true);
     if (st != BSFP_OK) return st;
     const int64_t tiles = (po.args.S + e->stream_tw - 1) / e->stream_tw;
     if (po.wpt != VARIANT_STREAMED || withhold_tile < -1 || withhold_tile >= tiles) return BSFP_ERR_SIZE;
