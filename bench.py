@@ -102,8 +102,10 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling (every 200 ms) around the timed region; the
+    summary keeps the samples whose timestamps fall inside it (mark_start /
+    mark_end), and says so, falling back to all samples if none does."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -111,6 +113,7 @@ class Clocks:
         self.path = tempfile.mktemp(suffix=".csv")
         self.proc = None
         self.gpu = gpu_index
+        self.t_start = self.t_end = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
@@ -118,6 +121,20 @@ class Clocks:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark_start(self):
+        self.t_start = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
+
+    @staticmethod
+    def _when(stamp: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if self.proc is None:
@@ -132,17 +149,23 @@ class Clocks:
         with open(self.path) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = rows
+        in_region = False
+        if self.t_start is not None and self.t_end is not None:
+            sel = [r for r in rows if (self._when(r[0]) or 0) >= self.t_start and (self._when(r[0]) or 0) <= self.t_end]
+            if sel:
+                inside, in_region = sel, True
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside), "samples_in_timed_region": in_region}
 
 
 def lop3_rate(bs, torch) -> float:
@@ -318,11 +341,15 @@ def run_gpu(args):
     torch.cuda.synchronize()
     launches0 = bs.bsfp_launch_count()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.mark_start()
     t0.record(stream)
     for k in range(args.steps):
         step(evs[k])
     t1.record(stream)
     torch.cuda.synchronize()
+    if clocks:
+        clocks.mark_end()
     launches = bs.bsfp_launch_count() - launches0
     if world > 1:
         dist.barrier()
@@ -767,7 +794,8 @@ def run_e2e(bs, torch, n, rank, args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000,
+                    help="timed steps (the default spans about 0.7 s, several clock samples)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["bsfp", "reference"], default="bsfp")
     ap.add_argument("--n", type=int, default=N, help="elements per vector (default 2^28)")
