@@ -73,7 +73,7 @@ typedef enum {
     BSFP_ERR_NULL = -2,        /* required pointer is NULL */
     BSFP_ERR_ALIGN = -3,       /* pointer not aligned as required */
     BSFP_ERR_SIZE = -4,        /* n < 0 or n > BSFP_MAX_N, or a bad count */
-    BSFP_ERR_UNSUPPORTED = -5, /* valid request that this build does not cover */
+    BSFP_ERR_UNSUPPORTED = -5, /* valid request that the compiled library does not cover */
     BSFP_ERR_CUDA = -6,        /* a CUDA call failed; see bsfp_last_cuda_error */
     BSFP_ERR_BUDGET = -7,      /* a request larger than a server's whole budget */
     BSFP_ERR_TIMEOUT = -8      /* a bounded wait ran out */
@@ -289,7 +289,7 @@ bsfp_status bsfp_pipeline_create(int64_t chunk, int32_t depth, bsfp_pipeline* ou
  * read only when some op is BSFP_OP_FMA2).  a, b, c, outs[q]: standard
  * arrays (containers of bsfp_container_bytes(f)) in host memory; page-locked
  * memory lets the copies run asynchronously, pageable memory works but its
- * copies are staged by the driver and overlap less.  Blocks until every
+ * copies are staged by the CUDA driver and overlap less.  Blocks until every
  * result is in host memory.  Errors: as the single ops, before any copy;
  * CUDA failures BSFP_ERR_CUDA. */
 bsfp_status bsfp_pipeline_run(bsfp_pipeline p, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,

@@ -490,7 +490,7 @@ const char* bsfp_status_str(int32_t status) {
         case BSFP_ERR_NULL: return "null pointer";
         case BSFP_ERR_ALIGN: return "misaligned pointer (bitslice: 16 bytes; standard: container size)";
         case BSFP_ERR_SIZE: return "size out of range";
-        case BSFP_ERR_UNSUPPORTED: return "not compiled into this build";
+        case BSFP_ERR_UNSUPPORTED: return "not compiled into the library";
         case BSFP_ERR_CUDA: return "CUDA error";
         case BSFP_ERR_BUDGET: return "over the memory budget";
         case BSFP_ERR_TIMEOUT: return "timed out";
