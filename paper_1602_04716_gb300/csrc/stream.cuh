@@ -22,9 +22,10 @@
  * The ring keeps NST tiles of loads in flight whatever the consumers are
  * doing, and the consumers never wait on global memory.  Tiles go to blocks
  * round-robin (tile t to block t mod gridDim).  Shapes (consumer warps x
- * stages) are fixed per plane count B so that the registers of NC+1 warps
- * and the ring fit one SM: 16 x 3 for B <= 9, 15 x 2 for B = 13, 12 x 2 for
- * B = 16 (measured against neighbouring shapes on 2^28-element operands).
+ * stages) are fixed per plane count B and op class so that the registers of
+ * NC+1 warps and the ring fit one SM: 16 x 3 for B <= 9, 15 x 2 for B = 13,
+ * 12 x 2 for B = 16 and 14 x 2 for mul 1/8/7 (measured against neighbouring
+ * shapes on 2^28-element operands).
  *
  * Waits are bounded (tma.cuh); a block whose wait gives up stops, lets its
  * copies in flight land, and sets *p.fault, which bsfp_fault_status reports.
@@ -45,11 +46,15 @@ namespace bsfp {
 constexpr bool stream_format(int E, int M) { return tuned_format(E, M) && 1 + E + M <= 16; }
 constexpr bool stream_opc(int opc) { return opc == OPC_ADDSUB || opc == OPC_MUL; }
 
-template <int E, int M>
+template <int E, int M, int OPC>
 struct StreamShape {
     static constexpr int B = 1 + E + M;
     static constexpr int WPT = 2;                                   /* words per consumer thread */
-    static constexpr int NC = B <= 9 ? 16 : (B <= 13 ? 15 : 12);    /* consumer warps */
+    /* consumer warps: 16 x 3 stages for B <= 9, 15 x 2 for B = 13, 12 x 2
+     * for B = 16 -- except mul 1/8/7, 14 x 2 (measured: 14 warps feed its
+     * logic pipe better; 1/5/10 mul gained nothing and its job-list form
+     * spills there, and the adders stream at the copy bandwidth with 12) */
+    static constexpr int NC = B <= 9 ? 16 : (B <= 13 ? 15 : ((OPC == OPC_MUL && E == 8) ? 14 : 12));
     static constexpr int NST = B <= 9 ? 3 : 2;                      /* ring stages */
     static constexpr int NIN = 2 * B;                               /* input planes per tile */
     static constexpr int TW = 32 * NC * WPT;                        /* words per plane per tile */
@@ -65,8 +70,8 @@ struct StreamShape {
  * 65536 / THREADS.  Adding a minimum of one block per SM changes ptxas's
  * register target and schedule and made the adders about 9% slower. */
 template <int E, int M, int R, int OPC>
-__global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_kernel(const BinopArgs p) {
-    using SH = StreamShape<E, M>;
+__global__ void __launch_bounds__(StreamShape<E, M, OPC>::THREADS) stream_kernel(const BinopArgs p) {
+    using SH = StreamShape<E, M, OPC>;
     constexpr int B = SH::B, NC = SH::NC, NST = SH::NST, NIN = SH::NIN, TW = SH::TW, WPT = SH::WPT;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -173,9 +178,9 @@ struct StreamTileMeta {
     uint32_t negb;
 };
 
-template <int E, int M>
+template <int E, int M, int OPC>
 struct StreamBatchShape {
-    using SH = StreamShape<E, M>;
+    using SH = StreamShape<E, M, OPC>;
     static constexpr int HDR = 256;   /* barriers, then one metadata slot per stage */
     static constexpr int META_OFF = 64;
     static constexpr size_t SMEM = HDR + (size_t)SH::NST * SH::NIN * SH::TW * 4;
@@ -185,10 +190,10 @@ struct StreamBatchShape {
 };
 
 template <int E, int M, int R, int OPC>
-__global__ void __launch_bounds__(StreamShape<E, M>::THREADS) stream_batch_kernel(
+__global__ void __launch_bounds__(StreamShape<E, M, OPC>::THREADS) stream_batch_kernel(
     const StreamJob* __restrict__ jobs, const int32_t* __restrict__ tile_job, int64_t ntiles, int* fault) {
-    using SH = StreamShape<E, M>;
-    using SB = StreamBatchShape<E, M>;
+    using SH = StreamShape<E, M, OPC>;
+    using SB = StreamBatchShape<E, M, OPC>;
     constexpr int B = SH::B, NC = SH::NC, NST = SH::NST, NIN = SH::NIN, TW = SH::TW, WPT = SH::WPT;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -281,19 +286,19 @@ template <int E, int M, int R, int OPC>
 cudaError_t stream_batch_launch(const StreamJob* jobs, const int32_t* tile_job, int64_t ntiles, int* fault, int grid,
                                 cudaStream_t s) {
     stream_batch_kernel<E, M, R, OPC>
-        <<<grid, StreamShape<E, M>::THREADS, StreamBatchShape<E, M>::SMEM, s>>>(jobs, tile_job, ntiles, fault);
+        <<<grid, StreamShape<E, M, OPC>::THREADS, StreamBatchShape<E, M, OPC>::SMEM, s>>>(jobs, tile_job, ntiles, fault);
     return cudaGetLastError();
 }
 
 template <int E, int M, int R, int OPC>
 cudaError_t stream_batch_prepare() {
     return cudaFuncSetAttribute(stream_batch_kernel<E, M, R, OPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)StreamBatchShape<E, M>::SMEM);
+                                (int)StreamBatchShape<E, M, OPC>::SMEM);
 }
 
 template <int E, int M, int R, int OPC>
 cudaError_t stream_launch(const BinopArgs& p, int grid, cudaStream_t s) {
-    using SH = StreamShape<E, M>;
+    using SH = StreamShape<E, M, OPC>;
     stream_kernel<E, M, R, OPC><<<grid, SH::THREADS, SH::SMEM, s>>>(p);
     return cudaGetLastError();
 }
@@ -302,7 +307,7 @@ cudaError_t stream_launch(const BinopArgs& p, int grid, cudaStream_t s) {
 template <int E, int M, int R, int OPC>
 cudaError_t stream_prepare() {
     return cudaFuncSetAttribute(stream_kernel<E, M, R, OPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)StreamShape<E, M>::SMEM);
+                                (int)StreamShape<E, M, OPC>::SMEM);
 }
 
 }  // namespace bsfp
