@@ -507,7 +507,7 @@ def run_batched(bs, torch, args, rank, hbm):
     wpt, bps = (args.batch_wpt, 0) if args.batch_wpt else tune.batch_shape()
     persistent = bs.BatchPlan(arr, nj, bs.BATCH_PERSISTENT, wpt, bps)
     variants["persistent_graph"] = timed(lambda: persistent.run(stream), args.batch_steps)
-    streamed = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    streamed = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED, wpt, bps)   # its persistent part takes the tuned shape
     variants["streamed_graph"] = timed(lambda: streamed.run(stream), args.batch_steps)
     plain_graph = bs.BatchPlan(arr, nj, bs.BATCH_PLAIN)
     variants["plain_graph"] = timed(lambda: plain_graph.run(stream), args.batch_steps)

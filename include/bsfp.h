@@ -209,7 +209,10 @@ typedef struct {
  * kernel in the same graph.  In BSFP_BATCH_STREAMED mode the add/sub and mul
  * jobs of those formats, in every rounding mode, go instead to one streamed
  * kernel per (format, rounding, op class), whose blocks take the tiles of
- * all its jobs round-robin.  The plan owns a device buffer (job descriptors, the tile-to-
+ * all its jobs round-robin.  The RN/RZ groups do so when they hold at least
+ * 8 tiles per SM on average (bsfp_set_batch_stream_min_tiles); otherwise
+ * they all stay with the persistent kernels.  Flush-to-zero groups, which
+ * the persistent kernels do not cover, always stream.  The plan owns a device buffer (job descriptors, the tile-to-
  * job map and the counters, allocated here) and a CUDA graph capturing
  * counter reset + kernels; it keeps the job pointers, which must stay valid
  * while the plan is run.  opt may be NULL.  Validation errors (any job)
@@ -220,6 +223,10 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
 /* Launch the plan's graph on stream s.  Runs of one plan must not overlap on
  * the GPU (they share the tile counters): use one stream per plan. */
 bsfp_status bsfp_batch_run(bsfp_batch_plan plan, bsfp_stream_t s);
+/* Minimum mean tiles per SM per RN/RZ group for a BSFP_BATCH_STREAMED plan
+ * to stream them (default 8; 0 = always).  Applies to plans created
+ * afterwards.  BSFP_ERR_SIZE outside [0, 2^20].  Not in the paper. */
+bsfp_status bsfp_set_batch_stream_min_tiles(int32_t tiles_per_sm);
 /* Kernel launches one run of the plan performs. */
 int64_t bsfp_batch_launches(bsfp_batch_plan plan);
 /* Release the plan; the caller must make sure no run of it is in flight. */

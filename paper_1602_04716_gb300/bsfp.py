@@ -132,6 +132,7 @@ def _lib():
                 "bsfp_fault_status": (i32, [i32]),
                 "bsfp_variant_for": (i32, [F, i32, i64]),
                 "bsfp_set_stream_min_tiles": (i32, [i32]),
+                "bsfp_set_batch_stream_min_tiles": (i32, [i32]),
                 "bsfp_stream_selftest": (i32, [F, i32, p, p, p, i64, i64, i64, p]),
                 "bsfp_synth_fp_values": (i32, [F, i64, u64, u64, i64, p, p]),
                 "bsfp_lop3_probe": (i32, [p, i32, i32, i32, u32, p]),
@@ -333,6 +334,10 @@ def bsfp_stream_selftest(f, op, a, b, out, n: int, withhold_tile: int, wait_cycl
     (the failure path of its bounded waits)."""
     _check(_lib().bsfp_stream_selftest(_fmt(f), OPS.get(op, op), _ptr(a), _ptr(b), _ptr(out), n, withhold_tile,
                                        wait_cycles, _stream(stream)), "bsfp_stream_selftest")
+
+
+def bsfp_set_batch_stream_min_tiles(tiles_per_sm: int):
+    _check(_lib().bsfp_set_batch_stream_min_tiles(tiles_per_sm), "bsfp_set_batch_stream_min_tiles")
 
 
 def bsfp_set_stream_min_tiles(tiles_per_sm: int):

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "batch.cuh"
@@ -43,6 +44,12 @@ const void* batch_kernel_ptr(int opc, int wpt) {
 }  // namespace bsfp
 
 using namespace bsfp;
+
+/* The RN/RZ groups of a BSFP_BATCH_STREAMED plan run as streamed kernels only
+ * with at least this many tiles per SM per group on average; otherwise they
+ * go to the persistent kernels, whose two launches cost less than ramping up
+ * and draining a launch per group (measured crossover between 5 and 10). */
+static std::atomic<int32_t> g_batch_stream_min_tiles{8};
 
 struct bsfp_batch_plan_st {
     void* dev = nullptr;           /* descriptors | tile maps | counters */
@@ -85,6 +92,9 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     struct SGroup {
         const BinopEntry* e;
         int* fault;
+        bool persistent_ok;           /* RN/RZ: the persistent kernels cover it */
+        int64_t tiles = 0;
+        std::vector<int32_t> members; /* job indices */
         std::vector<StreamJob> jobs;
         std::vector<int32_t> tmap;
     };
@@ -99,27 +109,56 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
             (po.entry->wpt_mask & (unsigned)VARIANT_STREAMED) && po.entry->stream_batch_launch) {
             size_t gi = 0;
             while (gi < sgroups.size() && sgroups[gi].e != po.entry) ++gi;
-            if (gi == sgroups.size()) sgroups.push_back(SGroup{po.entry, po.args.fault, {}, {}});
-            SGroup& g = sgroups[gi];
-            const BinopArgs& a = po.args;
-            StreamJob sj;
-            sj.a = a.a;
-            sj.b = a.b;
-            sj.out = a.out;
-            sj.S = a.S;
-            sj.nwords = a.nwords;
-            sj.tile0 = (int64_t)g.tmap.size();
-            sj.tailmask = a.tailmask;
-            sj.negb = a.negb;
-            const int64_t nt = (a.S + po.entry->stream_tw - 1) / po.entry->stream_tw;
-            const int32_t idx = (int32_t)g.jobs.size();
-            g.jobs.push_back(sj);
-            for (int64_t t = 0; t < nt; ++t) g.tmap.push_back(idx);
+            if (gi == sgroups.size())
+                sgroups.push_back(SGroup{po.entry, po.args.fault,
+                                         batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0});
+            sgroups[gi].members.push_back(i);
+            sgroups[gi].tiles += (po.args.S + po.entry->stream_tw - 1) / po.entry->stream_tw;
             group[(size_t)i] = OPC_COUNT;   /* handled by a streamed group */
             continue;
         }
         if (o.mode != BSFP_BATCH_PLAIN && po.opc < OPC_COUNT && batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0)
             group[(size_t)i] = po.opc;
+    }
+    /* one choice for the whole plan: the RN/RZ groups stream when they have
+     * at least min tiles per SM on average, else they all go to the
+     * persistent kernels (streaming only some of them adds launches whose
+     * ramp-up and drain the rest does not hide); the other groups stream */
+    {
+        const int64_t min_tiles =
+            (int64_t)g_batch_stream_min_tiles.load(std::memory_order_relaxed) * device_num_sms();
+        int64_t tiles = 0, ngroups = 0;
+        for (const SGroup& g : sgroups)
+            if (g.persistent_ok) {
+                tiles += g.tiles;
+                ++ngroups;
+            }
+        const bool stream_rnrz = ngroups == 0 || tiles >= min_tiles * ngroups;
+        std::vector<SGroup> kept;
+        for (SGroup& g : sgroups) {
+            if (g.persistent_ok && !stream_rnrz) {
+                for (int32_t i : g.members) group[(size_t)i] = prep[(size_t)i].opc;
+                continue;
+            }
+            for (int32_t i : g.members) {
+                const BinopArgs& a = prep[(size_t)i].args;
+                StreamJob sj;
+                sj.a = a.a;
+                sj.b = a.b;
+                sj.out = a.out;
+                sj.S = a.S;
+                sj.nwords = a.nwords;
+                sj.tile0 = (int64_t)g.tmap.size();
+                sj.tailmask = a.tailmask;
+                sj.negb = a.negb;
+                const int64_t nt = (a.S + g.e->stream_tw - 1) / g.e->stream_tw;
+                const int32_t idx = (int32_t)g.jobs.size();
+                g.jobs.push_back(sj);
+                for (int64_t t = 0; t < nt; ++t) g.tmap.push_back(idx);
+            }
+            kept.push_back(std::move(g));
+        }
+        sgroups.swap(kept);
     }
     for (SGroup& g : sgroups) {
         const cudaError_t e = g.e->stream_batch_prepare();
@@ -301,6 +340,12 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         return st;
     }
     *plan_out = p;
+    return BSFP_OK;
+}
+
+bsfp_status bsfp_set_batch_stream_min_tiles(int32_t tiles_per_sm) {
+    if (tiles_per_sm < 0 || tiles_per_sm > 1 << 20) return BSFP_ERR_SIZE;
+    g_batch_stream_min_tiles.store(tiles_per_sm, std::memory_order_relaxed);
     return BSFP_OK;
 }
 

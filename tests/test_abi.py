@@ -91,6 +91,9 @@ def test_stream_threshold_and_variant_query_arguments():
     assert L.bsfp_set_stream_min_tiles(-1) == bs.ERR_SIZE
     assert L.bsfp_set_stream_min_tiles(1025) == bs.ERR_SIZE
     assert L.bsfp_set_stream_min_tiles(2) == bs.OK
+    assert L.bsfp_set_batch_stream_min_tiles(-1) == bs.ERR_SIZE
+    assert L.bsfp_set_batch_stream_min_tiles((1 << 20) + 1) == bs.ERR_SIZE
+    assert L.bsfp_set_batch_stream_min_tiles(8) == bs.OK
     assert bs.bsfp_variant_for(bs.Format(9, 7), "mul", 10) == -1
     assert bs.bsfp_variant_for(bs.Format(5, 7), 9, 10) == -1
     assert bs.bsfp_variant_for(bs.Format(5, 7), "mul", -1) == -1

@@ -96,7 +96,11 @@ def test_streamed_plan_matches_oracle_and_replays():
     replay of the graph."""
     jobs = _make_batch(220, 5100)
     arr, nj = _ctypes_jobs(jobs)
-    plan = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    bs.bsfp_set_batch_stream_min_tiles(0)   # every group streamed, however small
+    try:
+        plan = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    finally:
+        bs.bsfp_set_batch_stream_min_tiles(8)
     groups = {(j["E"], j["M"], j["rnd"], j["op"] == "mul") for j in jobs
               if (j["E"], j["M"]) in bs.BATCH_FORMATS and j["op"] in ("add", "sub", "mul") and j["n"] > 0}
     n_plain = sum(1 for j in jobs if j["n"] > 0 and ((j["E"], j["M"]) not in bs.BATCH_FORMATS or j["op"] == "div" or
@@ -121,11 +125,39 @@ def test_streamed_plan_many_tiles_per_block():
         if j["op"] in ("fma2", "div"):
             j["op"] = "mul"
     arr, nj = _ctypes_jobs(jobs)
-    plan = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    bs.bsfp_set_batch_stream_min_tiles(0)
+    try:
+        plan = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    finally:
+        bs.bsfp_set_batch_stream_min_tiles(8)
     plan.run()
     torch.cuda.synchronize()
     _check_all(jobs)
     assert bs.bsfp_fault_status() == 0
+    plan.free()
+
+
+def test_streamed_plan_sends_small_groups_to_the_persistent_kernels():
+    """With the default threshold (8 tiles per SM per group on average) the
+    RN/RZ groups of a small batch all run in the persistent kernels (one
+    launch per op class); the flush-to-zero groups, which the persistent
+    kernels do not cover, stay streamed.  Every job exact."""
+    jobs = _make_batch(220, 5200)
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED)
+    live = [j for j in jobs if j["n"] > 0]
+    batch = [j for j in live if (j["E"], j["M"]) in bs.BATCH_FORMATS]
+    stream_groups = {(j["E"], j["M"], j["rnd"], j["op"] == "mul") for j in batch
+                     if j["op"] in ("add", "sub", "mul") and j["rnd"] > 1}
+    persistent = {("mul" if j["op"] == "mul" else "fma2" if j["op"] == "fma2" else "add") for j in batch
+                  if j["op"] in ("add", "sub", "mul", "fma2") and j["rnd"] < 2}
+    plain = [j for j in live if (j["E"], j["M"]) not in bs.BATCH_FORMATS or j["op"] == "div" or
+             (j["op"] == "fma2" and j["rnd"] > 1)]
+    assert plan.launches == len(stream_groups) + len(persistent) + len(plain)
+    _clear(jobs)
+    plan.run()
+    torch.cuda.synchronize()
+    _check_all(jobs)
     plan.free()
 
 
