@@ -54,10 +54,11 @@ WORKLOAD = ("plain single-format at scale: bs_add + bs_mul (RN) on 1/4/4 and 1/5
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from ncu captures at 2^26 elements
 # scaled x4 to the 2^28-element launch, keyed by (E, M, op, kernel variant): a figure stands only
 # for the kernel it was taken on (profiles/stream_mul_1_5_7_full_2p26.md,
-# profiles/binop_1_5_7_add_mul_full_2p26.md).
+# profiles/traffic_bench_kernels_2p26.md).
 NCU_TRAFFIC = {(5, 7, "mul", 8): (218.137344e6 + 67.117568e6) * 4,
                (5, 7, "mul", 4): (218.150656e6 + 70.085376e6) * 4,
-               (5, 7, "add", 2): (218.121216e6 + 71.256576e6) * 4}
+               (5, 7, "add", 2): (218.126592e6 + 70.077952e6) * 4,
+               (4, 4, "mul", 8): (151.011072e6 + 34.781184e6) * 4}
 
 
 class DeviceTimer:
