@@ -47,16 +47,11 @@ RND = 0
 WORKLOAD = ("plain single-format at scale: bs_add + bs_mul (RN) on 1/4/4 and 1/5/7, "
             "2^28 elements per vector, operands resident in bitslice form")
 
-# dram__bytes_read.sum + dram__bytes_write.sum per 2^28-element launch, keyed
-# by (E, M, op), from the ncu capture of the kernel as it now stands at 2^26
-# elements scaled by 4 (profiles/binop_1_5_7_add_mul_full_2p26.md); a kernel
-# not listed, or changed since its capture, reports null.
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from ncu captures at 2^26 elements
 # scaled x4 to the 2^28-element launch, keyed by (E, M, op, kernel variant): a figure stands only
-# for the kernel it was taken on (profiles/stream_mul_1_5_7_full_2p26.md,
-# profiles/traffic_bench_kernels_2p26.md).
+# for the kernel it was taken on, as it now stands (profiles/stream_mul_1_5_7_full_2p26.md,
+# profiles/traffic_bench_kernels_2p26.md); a kernel not listed reports null.
 NCU_TRAFFIC = {(5, 7, "mul", 8): (218.137344e6 + 67.117568e6) * 4,
-               (5, 7, "mul", 4): (218.150656e6 + 70.085376e6) * 4,
                (5, 7, "add", 2): (218.126592e6 + 70.077952e6) * 4,
                (4, 4, "mul", 8): (151.011072e6 + 34.781184e6) * 4}
 
