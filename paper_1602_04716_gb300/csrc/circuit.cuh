@@ -156,8 +156,8 @@ BSFP_HDC constexpr int floor_log2(int v) { return v <= 1 ? 0 : 1 + floor_log2(v 
  * bits of z are zero and the remaining budget allows it.  The budget test is
  * u >= (t[KT..K+1], 1, 0..0), i.e. u - (shift already taken) >= S, done as a
  * borrow chain over bits K..KT of u; hiu = some bit of u above KT is set. */
-template <int N, int NU, int KT, int K, class W>
-BSFP_HD void ln_stage(W* z, const W* u, W hiu, W* t) {
+template <int N, int NU, int KT, int K, int LO, class W>
+BSFP_HD void ln_stage(W* z, const W* u, W hiu, W* t, W* st) {
     constexpr int S = 1 << K;
     W c;
     if constexpr (K >= NU) {
@@ -172,24 +172,39 @@ BSFP_HD void ln_stage(W* z, const W* u, W hiu, W* t) {
     t[K] = c;
     BSFP_UNROLL
     for (int p = N - 1; p >= 0; --p) z[p] = MUX(c, (p >= S) ? z[(p >= S) ? p - S : 0] : W(0u), z[p]);
+    /* the later stages shift by at most S - 1 more, so a position p <= LO - S
+     * ends below LO whatever they do: it only counts through the sticky OR.
+     * Fold it into *st and clear it (bits only move up, so nothing above
+     * depends on it), and the later stages' multiplexers on zeros vanish. */
+    if constexpr (LO > 0) {
+        BSFP_UNROLL
+        for (int p = 0; p <= LO - S && p < N; ++p) {
+            *st = OR(*st, z[p]);
+            z[p] = W(0u);
+        }
+    }
 }
 
-template <int N, int NU, int KT, int K, class W>
-BSFP_HD void ln_stages(W* z, const W* u, W hiu, W* t) {
-    ln_stage<N, NU, KT, K>(z, u, hiu, t);
-    if constexpr (K > 0) ln_stages<N, NU, KT, K - 1>(z, u, hiu, t);
+template <int N, int NU, int KT, int K, int LO, class W>
+BSFP_HD void ln_stages(W* z, const W* u, W hiu, W* t, W* st) {
+    ln_stage<N, NU, KT, K, LO>(z, u, hiu, t, st);
+    if constexpr (K > 0) ln_stages<N, NU, KT, K - 1, LO>(z, u, hiu, t, st);
 }
 
 /* Normalise z (N words, z[N-1] = top) left by t = min(lz(z), u) where u is an
  * unsigned NU-bit budget; writes the shift t[0..KT], KT = floor(log2(N-1)).
  * Greedy from the largest stage down: each stage removes 2^K leading zeros
  * when both the zeros and the budget allow, which decomposes min(lz, u)
- * exactly (the normalisation log shifter of Sec. 4, Table 1). */
-template <int N, int NU, class W> BSFP_HD void lnorm(W* z, const W* u, W* t) {
+ * exactly (the normalisation log shifter of Sec. 4, Table 1).
+ * LO > 0: the caller uses positions below LO of the result only through
+ * their OR (a sticky bit); they are OR-ed into *st (which the caller
+ * initialises) as soon as no later stage can lift them to LO, and left
+ * zero. */
+template <int N, int NU, int LO = 0, class W> BSFP_HD void lnorm(W* z, const W* u, W* t, W* st = nullptr) {
     constexpr int KT = floor_log2(N - 1);
     W hiu = W(0u);
     if constexpr (KT + 1 < NU) hiu = or_n<NU - KT - 1>(u + KT + 1);
-    ln_stages<N, NU, KT, KT>(z, u, hiu, t);
+    ln_stages<N, NU, KT, KT, LO>(z, u, hiu, t, st);
 }
 
 /* D = u - t (u: NU bits, t: NT bits, u >= t), NU-bit result. */
@@ -353,14 +368,15 @@ BSFP_HD void fp_add(const W* a, const W* b, W* r) {
     for (int i = 1; i < E; ++i) u[i] = eX[i];
     constexpr int KT = floor_log2(NZ - 1);
     W t[KT + 1];
-    lnorm<NZ, E>(z, u, t);
+    W stz = W(0u);                   /* sticky of the positions below the guard */
+    lnorm<NZ, E, 3>(z, u, t, &stz);
     W D[E];
     sub_un<E, KT + 1>(u, t, D);
 
     /* step 5 (rounding): significand z[M+4..4], guard z[3], sticky z[2..0] */
     const W* sig = z + 4;
     W rup = W(0u);
-    if constexpr (!RZ) rup = F3<LUT_G_AND_LS>(z[3], sig[0], OR3(z[2], z[1], z[0]));
+    if constexpr (!RZ) rup = F3<LUT_G_AND_LS>(z[3], sig[0], OR(stz, OR3(z[2], z[1], z[0])));
     W mag[M + E + 1];
     assemble<M, E>(D, sig, rup, mag);
 
@@ -570,7 +586,8 @@ template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void fp_mul(
     for (int i = 0; i < NU - 1; ++i) um[i] = ANDN(u[i], neg);    /* budget 0 when u < 0 */
     constexpr int KT = floor_log2(NP - 1);
     W t[KT + 1];
-    lnorm<NP, NU - 1>(zl, um, t);
+    W stl = W(0u);                   /* sticky of the positions below the guard zl[M] */
+    lnorm<NP, NU - 1, M>(zl, um, t, &stl);
     W D[NU - 1];
     sub_un<NU - 1, KT + 1>(um, t, D);
 
@@ -597,7 +614,7 @@ template <int E, int M, bool RZ, bool FTZ = false, class W> BSFP_HD void fp_mul(
     W rup = W(0u);
     if constexpr (!RZ) {
         const W g = MUX(neg, q[1], zl[M]);
-        const W st = MUX(neg, q[0], or_n<M>(zl));
+        const W st = MUX(neg, q[0], OR(stl, or_n<M>(zl)));
         rup = F3<LUT_G_AND_LS>(g, sig[0], st);
     }
 
