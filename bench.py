@@ -738,6 +738,29 @@ def run_sweep(bs, torch, args, rank, hbm, L):
     return summary
 
 
+def host_link_rates(torch, pinned, reps=3):
+    """Plain copy rates of this machine's host link: one page-locked host buffer
+    to the device and back, best of `reps` (CUDA events on the current
+    stream).  Recorded beside the end-to-end figure, which the link bounds,
+    so that the end-to-end numbers of different boxes can be compared."""
+    dev = torch.empty_like(pinned, device="cuda")
+    nbytes = pinned.numel() * pinned.element_size()
+    best = {"h2d": float("inf"), "d2h": float("inf")}
+    for _ in range(reps):
+        for kind in ("h2d", "d2h"):
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            if kind == "h2d":
+                dev.copy_(pinned, non_blocking=True)
+            else:
+                pinned.copy_(dev, non_blocking=True)
+            t1.record()
+            t1.synchronize()
+            best[kind] = min(best[kind], t0.elapsed_time(t1))
+    del dev
+    return {"bytes": nbytes, "h2d_gbs": nbytes / best["h2d"] / 1e6, "d2h_gbs": nbytes / best["d2h"] / 1e6}
+
+
 def run_e2e(bs, torch, n, rank, args):
     """Per step, for both formats: the two operand vectors in page-locked host
     memory (standard form) through bsfp_pipeline_run -- chunked copy in, pack,
@@ -780,8 +803,11 @@ def run_e2e(bs, torch, n, rank, args):
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t) / k
     pipe.close()
+    link = host_link_rates(torch, host_in[FORMATS[-1]][0])
+    link_ms = 1e3 * (h2d / (link["h2d_gbs"] * 1e9) + d2h / (link["d2h_gbs"] * 1e9))
+    link["serial_copy_ms_per_step"] = link_ms
     return {"value": len(FORMATS) * len(OPS) * n / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k,
+            "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k, "host_link": link,
             "path": "pinned host -> bsfp_pipeline_run (chunks of %d over %d streams: H2D, bsfp_pack, "
                     "bsfp_add + bsfp_mul, bsfp_unpack, D2H) -> pinned host, per format"
                     % (args.e2e_chunk or (1 << 23), args.e2e_depth or 4)}
