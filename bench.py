@@ -106,12 +106,12 @@ class Clocks:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.path = tempfile.mktemp(suffix=".csv")
         self.proc = None
         self.gpu = gpu_index
         self.t_start = self.t_end = None
+        self.fh = tempfile.NamedTemporaryFile("w", suffix=".csv", delete=False)
+        self.path = self.fh.name
         try:
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -134,6 +134,8 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            self.fh.close()
+            os.unlink(self.path)
             return None
         self.proc.terminate()
         try:
