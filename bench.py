@@ -49,11 +49,10 @@ WORKLOAD = ("plain single-format at scale: bs_add + bs_mul (RN) on 1/4/4 and 1/5
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from ncu captures at 2^26 elements
 # scaled x4 to the 2^28-element launch, keyed by (E, M, op, kernel variant): a figure stands only
-# for the kernel it was taken on, as it now stands (profiles/stream_mul_1_5_7_full_2p26.md,
-# profiles/traffic_bench_kernels_2p26.md); a kernel not listed reports null.
-# The captures there were taken before the sticky-collapsing normaliser changed the circuits of all
-# four bench kernels (same data movement, fewer gates), so no entry stands for them now.
-NCU_TRAFFIC = {}
+# for the kernel it was taken on, as it now stands (profiles/traffic_bench_kernels_2p26.md: medians of
+# five launches each); a kernel not listed reports null.
+NCU_TRAFFIC = {(5, 7, "add", 2): (218.124544e6 + 69.806080e6) * 4,
+               (5, 7, "mul", 8): (218.133504e6 + 63.068928e6) * 4}
 
 
 class DeviceTimer:
