@@ -264,3 +264,27 @@ def test_batch_plan_options_validated_before_any_cuda_call():
         assert L.bsfp_batch_plan_create(None, 0, ctypes.byref(opt), ctypes.byref(h)) == bs.ERR_SIZE
     assert L.bsfp_batch_plan_create(None, -1, None, ctypes.byref(h)) == bs.ERR_SIZE
     assert L.bsfp_batch_plan_create(None, 1, None, ctypes.byref(h)) == bs.ERR_NULL
+
+
+def test_tuning_cache_matches_the_build():
+    """Every per-format entry of the committed tuning cache names a variant
+    compiled for its (format, op), with a blocks-per-SM choice the tuner
+    offers; tune.apply() silently skips any other entry, so drift between the
+    cache and the build would otherwise show only as slower launches.  Each
+    GPU's cache covers every generated format in all four modes and op
+    classes."""
+    from paper_1602_04716_gb300 import build, tune
+    cache = tune.load()
+    assert cache, "no tuning cache committed"
+    for gpu, entries in cache.items():
+        keys = [k for k in entries if k.count("/") == 3]
+        for key in keys:
+            v = entries[key]
+            e, m, r, op = key.split("/")
+            f = bs.Format(int(e), int(m), int(r))
+            assert v["wpt"] in bs.bsfp_variants_compiled(f, op), (gpu, key, v)
+            assert v["bps"] in (0, 1, 2, 3, 4, 6, 8), (gpu, key, v)
+            assert v["ms"] > 0 and v["n"] > 0, (gpu, key, v)
+        want = {"%d/%d/%d/%s" % (E, M, r, op) for E, M in build.GEN_FORMATS for r in range(4)
+                for op in ("add", "mul", "fma2", "div")}
+        assert want <= set(keys), (gpu, sorted(want - set(keys))[:8])
