@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the clock sampler's parsing,
 its restriction to the timed region and its throttle-reason report, driven
-by a stand-in nvidia-smi script that prints rows in the query's CSV format."""
+by a stand-in nvidia-smi script that prints rows in the query's CSV format;
+and the JSON line of the reference arm, which times the oracle on the host."""
 import os
 import stat
 import time
@@ -61,3 +62,27 @@ def test_clocks_without_nvidia_smi(tmp_path, monkeypatch):
     tmp = c.path
     assert c.stop() is None
     assert not os.path.exists(tmp)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the oracle on the host cores, bounded
+    samples) prints one JSON line with the keys of the bench contract, on
+    the same metric and unit as the GPU arm, and an e2e entry that moves no
+    bytes across the host link."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "3", "--warmup", "3", "--ref-sample", "4096"],
+                         capture_output=True, text=True, timeout=300, cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["steps"] == 3 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
