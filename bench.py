@@ -639,32 +639,53 @@ def run_integers(bs, torch, n, hbm, L):
 def run_small_case(bs, torch, rank):
     """The 8-bit format 1/4/3 on all 65,536 operand pairs (a = i >> 8,
     b = i & 255): bs_add and bs_mul, RN and RZ, plus the pack/unpack round
-    trip, as single launches; too small for a roofline, so latency only."""
-    import oracle  # noqa: F401  (the pairs are built here; parity is checked by the tests)
+    trip, as single launches; too small for a roofline, so latency only.
+
+    Three figures per kernel.  `us`: one launch between CUDA events after an
+    L2 flush (DeviceTimer), which carries the fixed device-side cost of any
+    launch.  `floor_us`: the same measurement of a one-element fill, the cost
+    of an empty launch; `over_floor_us` = `us` - `floor_us` is then the
+    kernel's own time.  `back_to_back_us`: 64 launches in a row between two
+    events, divided by 64 (warm L2, launch overheads overlapped)."""
     n = 1 << 16
     i = np.arange(n, dtype=np.uint32)
     out = {}
     stream = torch.cuda.current_stream()
     timer = DeviceTimer(torch, stream)
+    tiny = torch.empty(1, dtype=torch.int32, device="cuda")
+    floor = timer.ms(lambda: tiny.fill_(1), reps=20) * 1e3
+    out["floor_us"] = floor
+
+    def back_to_back(fn, k=64):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / k
+
+    def record(name, fn):
+        us = timer.ms(fn, reps=20) * 1e3
+        out[name] = {"us": us, "over_floor_us": us - floor, "back_to_back_us": back_to_back(fn)}
+
     for rnd in (0, 1):
         f = bs.Format(4, 3, rnd)
         std = [torch.from_numpy(x.astype(np.uint8)).cuda() for x in (i >> 8, i & 255)]
         planes = [bs.empty_bitslice(f, n) for _ in range(3)]
         back = bs.empty_standard(f, n)
-
-        def timed(fn):
-            return timer.ms(fn, reps=20) * 1e3
-
         r = "RZ" if rnd else "RN"
-        out["pack_us"] = timed(lambda: bs.bsfp_pack(f, std[0], n, planes[0], stream=stream))
+        record("pack", lambda: bs.bsfp_pack(f, std[0], n, planes[0], stream=stream))
         bs.bsfp_pack(f, std[1], n, planes[1], stream=stream)
         for op in ("add", "mul"):
-            out["%s_%s_us" % (op, r)] = timed(lambda: bs.bsfp_op(op, f, planes[0], planes[1], planes[2], n,
-                                                                 stream=stream))
-        out["unpack_us"] = timed(lambda: bs.bsfp_unpack(f, planes[0], n, back, stream=stream))
+            record("%s_%s" % (op, r), lambda: bs.bsfp_op(op, f, planes[0], planes[1], planes[2], n, stream=stream))
+        record("unpack", lambda: bs.bsfp_unpack(f, planes[0], n, back, stream=stream))
         assert torch.equal(back, std[0])
-    out["workload"] = ("1/4/3, all 65,536 operand pairs, single launches (median of 20, CUDA events around the "
-                       "kernel alone: L2 flushed and host launch latency excluded)")
+    out["workload"] = ("1/4/3, all 65,536 operand pairs, single launches: CUDA events around one launch after "
+                       "an L2 flush (median of 20; host launch latency excluded), the same for a one-element "
+                       "fill (floor_us), and 64 back-to-back launches per event pair")
     return out
 
 

@@ -449,7 +449,7 @@ int32_t bsfp_variant_for(bsfp_format f, int32_t op, int64_t n);
  * (format, op) has no streamed kernel; BSFP_ERR_SIZE for an out-of-range
  * tile or bound. */
 bsfp_status bsfp_stream_selftest(bsfp_format f, int32_t op, const uint32_t* a, const uint32_t* b, uint32_t* out,
-                                 int64_t n, int64_t withhold_tile, int64_t wait_cycles, cudaStream_t s);
+                                 int64_t n, int64_t withhold_tile, int64_t wait_cycles, bsfp_stream_t s);
 /* Minimum tiles per SM for the streamed variant (default 2; 0 = always take
  * it when selected).  Process-wide; BSFP_ERR_SIZE outside [0, 1024]. */
 bsfp_status bsfp_set_stream_min_tiles(int32_t tiles_per_sm);
