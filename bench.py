@@ -296,6 +296,8 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     tuned = apply_tuning()
     n = args.n
+    if args.section:
+        return run_section(bs, torch, args, rank)
 
     # ---- operands: drawn on the device, packed once, resident ----
     bufs = {}
@@ -432,6 +434,28 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def run_section(bs, torch, args, rank):
+    """One section of the bench on its own (for a profiler capture of its
+    kernels, or a quick look): prints one JSON line holding that section."""
+    hbm, _ = _peaks()
+    n = args.n
+    if args.section == "conversions":
+        res = run_conversions(bs, torch, n, hbm, reps=args.section_reps)
+    elif args.section == "small":
+        res = run_small_case(bs, torch, rank)
+    elif args.section == "integers":
+        res = run_integers(bs, torch, n, hbm, lop3_rate(bs, torch))
+    elif args.section == "sweep":
+        res = run_sweep(bs, torch, args, rank, hbm, lop3_rate(bs, torch))
+    elif args.section == "batched":
+        res = run_batched(bs, torch, args, rank, hbm)
+    else:
+        res = run_serving(bs, torch, args, rank)
+    if rank == 0:
+        print(json.dumps({"section": args.section, "elements_per_vector": n, args.section: res}), flush=True)
     return 0
 
 
@@ -576,7 +600,7 @@ def run_serving(bs, torch, args, rank):
     return out
 
 
-def run_conversions(bs, torch, n, hbm):
+def run_conversions(bs, torch, n, hbm, reps=5):
     """bsfp_from_float (binary32 -> planes, RN), bsfp_to_float (planes ->
     binary32), bsfp_pack and bsfp_unpack for the two formats of the workload
     at n elements: CUDA-event time (median of 5 after a warm-up, DeviceTimer) and
@@ -598,7 +622,7 @@ def run_conversions(bs, torch, n, hbm):
                 ("to_float", lambda: bs.bsfp_to_float(f, planes, n, back, stream=stream), 4),
                 ("pack", lambda: bs.bsfp_pack(f, std, n, planes, stream=stream), cb),
                 ("unpack", lambda: bs.bsfp_unpack(f, planes, n, std, stream=stream), cb)):
-            t = timer.ms(fn) * 1e-3
+            t = timer.ms(fn, reps=reps) * 1e-3
             gbs = n * (bpe + (1 + E + M) / 8) / t / 1e9
             out["%s 1/%d/%d" % (name, E, M)] = {"ms": t * 1e3, "elements_per_s": n / t, "hbm_gbs": gbs,
                                                 "hbm_frac": gbs / hbm}
@@ -864,6 +888,10 @@ def main(argv=None):
     ap.add_argument("--sweep-n", type=int, default=1 << 26,
                     help="elements per vector in the format sweep (0 skips it)")
     ap.add_argument("--sweep-out", default=None, help="write the full sweep table (JSON) here")
+    ap.add_argument("--section", default=None,
+                    choices=["conversions", "small", "integers", "sweep", "batched", "serving"],
+                    help="run only this section of the bench and print it (no main timed loop)")
+    ap.add_argument("--section-reps", type=int, default=5, help="timed launches per kernel in --section conversions")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -3,103 +3,151 @@
  * operands of a format 1/E/M (not the paper's operations: the step before
  * and after them when the data are ordinary floats).
  *
- * from_float: a warp owns 1024 elements (32 word columns).  For each of the
- * 32 element groups it loads 32 consecutive floats (binary32, or bfloat16 /
- * binary16 widened exactly to binary32 bit patterns), transposes the 32x32
- * bit matrix across the warp and stores the 32 slices of the group into
- * padded shared memory; then lane c holds the 32 binary32 slices of column
- * c, runs the narrowing circuit from_f32 (circuit.cuh) on whole words and
- * stores the B output planes, each a coalesced 128-byte row per warp.
+ * A warp owns a tile of 32 word columns (1024 elements) and each lane one
+ * column, as in pack/unpack (transpose.cu, bit_transpose.cuh).
+ *
+ * from_float: the tile's source values go to the warp's staging area in
+ * shared memory (coalesced 16-byte loads); each lane reads its column's 32
+ * values and transposes them in registers into 32 binary32 slices -- bfloat16
+ * sources transpose as 16-bit rows into slices 16..31 (slices 0..15 are
+ * zero), binary16 sources are widened exactly to binary32 value by value
+ * first -- then runs the narrowing circuit from_f32 (circuit.cuh) on whole
+ * words and stores the B output planes, a coalesced 128-byte row per warp.
  *
  * to_float: the reverse -- each lane loads the B planes of its column, runs
- * the exact widening circuit to_f32, the 32 result slices go through shared
- * memory and the warp transpose back to 32 binary32 values per group,
- * stored as coalesced rows.
+ * the exact widening circuit to_f32, transposes the 32 result slices into 32
+ * binary32 values in registers, and the warp stores the tile from the
+ * staging area with coalesced 16-byte stores.
  *
- * Elements past n are read as +0 (they become zero padding); outputs past n
- * are not written.
+ * The staged column sits in the lane's registers rotated by rho elements
+ * (bit_transpose.cuh); the element-wise circuits do not care, and each plane
+ * word is rotated back (or into place) by one funnel rotate.  Elements past n
+ * are read as +0 (they become zero padding); outputs past n are not written.
  */
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bit_transpose.cuh"
 #include "circuit.cuh"
-#include "warp_transpose.cuh"
 
 namespace bsfp {
 
 constexpr int CV_WARPS = 4;    /* warps per block */
-constexpr int CV_ROW = 33;     /* padded shared-memory row (words) */
 
 /* source element types of from_float (bsfp_float_type in bsfp.h) */
 enum : int { SRC_F32 = 0, SRC_BF16 = 1, SRC_F16 = 2 };
 
-__device__ __forceinline__ uint32_t load_as_f32_bits(const void* in, int src, int64_t i) {
-    if (src == SRC_F32) return __ldcs(static_cast<const uint32_t*>(in) + i);
-    if (src == SRC_BF16) return (uint32_t)__ldcs(static_cast<const unsigned short*>(in) + i) << 16;
-    const unsigned short h = __ldcs(static_cast<const unsigned short*>(in) + i);
-    return __float_as_uint(__half2float(__ushort_as_half(h)));
+/* The tile's 1024 source values (CB bytes each) into the staging area. */
+template <int CB>
+__device__ __forceinline__ void cv_stage_in(uint8_t* s, const void* in, int64_t e0, int64_t n, bool vec, int lane) {
+    if (vec && e0 + 1024 <= n) {
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(in) + e0 * CB);
+        uint4 v[2 * CB];
+#pragma unroll
+        for (int k = 0; k < 2 * CB; ++k) v[k] = __ldcs(src + lane + 32 * k);
+#pragma unroll
+        for (int k = 0; k < 2 * CB; ++k) reinterpret_cast<uint4*>(s)[lane + 32 * k] = v[k];
+    } else if constexpr (CB == 4) {
+        const uint32_t* src = static_cast<const uint32_t*>(in);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int64_t i = e0 + lane + 32 * k;
+            reinterpret_cast<uint32_t*>(s)[lane + 32 * k] = (i < n) ? __ldcs(src + i) : 0u;
+        }
+    } else {
+        const unsigned short* src = static_cast<const unsigned short*>(in);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int64_t i = e0 + lane + 32 * k;
+            reinterpret_cast<unsigned short*>(s)[lane + 32 * k] = (i < n) ? __ldcs(src + i) : (unsigned short)0;
+        }
+    }
 }
 
 template <int E, int M, int R>
 __global__ void __launch_bounds__(32 * CV_WARPS) from_float_kernel(const void* __restrict__ in, int src, int64_t n,
-                                                                   uint32_t* __restrict__ out, int64_t S) {
+                                                                   uint32_t* __restrict__ out, int64_t S, bool vec) {
     constexpr int B = 1 + E + M;
-    __shared__ uint32_t sm[CV_WARPS][32 * CV_ROW];
+    __shared__ __align__(16) uint8_t sm[CV_WARPS][4096];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* s = sm[warp];
+    uint8_t* s = sm[warp];
     const int64_t ntiles = S / 32;
     for (int64_t tile = (int64_t)blockIdx.x * CV_WARPS + warp; tile < ntiles;
          tile += (int64_t)gridDim.x * CV_WARPS) {
         const int64_t e0 = tile * 1024;
-        /* all 32 loads of the tile first, so that they are in flight together */
-        uint32_t v[32];
+        uint32_t x[32];
+        int rho;
+        if (src == SRC_F32) {
+            cv_stage_in<4>(s, in, e0, n, vec, lane);
+            __syncwarp();
+            stage_read_column<4>(s, lane, x);
+            transpose32(x);
+            rho = stage_rho<4>(lane);
+        } else {
+            cv_stage_in<2>(s, in, e0, n, vec, lane);
+            __syncwarp();
+            uint32_t w[16];
+            stage_read_column<2>(s, lane, w);
+            if (src == SRC_BF16) {
+                /* a bfloat16 is the top half of its binary32: slices 16..31
+                 * are the transposed 16-bit rows, slices 0..15 zero */
+                gather16(w, x + 16);
+                transpose16x2(x + 16);
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const int64_t i = e0 + (int64_t)t * 32 + lane;
-            v[t] = (i < n) ? load_as_f32_bits(in, src, i) : 0u;
+                for (int b = 0; b < 16; ++b) x[b] = 0u;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const unsigned short h = (unsigned short)((j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xFFFFu));
+                    x[j] = __float_as_uint(__half2float(__ushort_as_half(h)));
+                }
+                transpose32(x);
+            }
+            rho = stage_rho<2>(lane);
         }
-#pragma unroll
-        for (int t = 0; t < 32; ++t) s[lane * CV_ROW + t] = warp_transpose32(v[t], lane);   /* lane b: slice b */
-        __syncwarp();
-        uint32_t x[32], r[B];
-#pragma unroll
-        for (int b = 0; b < 32; ++b) x[b] = s[b * CV_ROW + lane];
+        __syncwarp();   /* the next tile may overwrite the staging area */
+        uint32_t r[B];
         from_f32<E, M, mode_rz(R), mode_ftz(R)>(x, r);
+        uint32_t* o = out + tile * 32 + lane;
 #pragma unroll
-        for (int b = 0; b < B; ++b) __stcs(out + b * S + tile * 32 + lane, r[b]);
-        __syncwarp();
+        for (int b = 0; b < B; ++b) __stcs(o + b * S, rotl32(r[b], rho));
     }
 }
 
 template <int E, int M, int R>
 __global__ void __launch_bounds__(32 * CV_WARPS) to_float_kernel(const uint32_t* __restrict__ in, int64_t S, int64_t n,
-                                                                 uint32_t* __restrict__ out) {
+                                                                 uint32_t* __restrict__ out, bool vec) {
     constexpr int B = 1 + E + M;
-    __shared__ uint32_t sm[CV_WARPS][32 * CV_ROW];
+    __shared__ __align__(16) uint8_t sm[CV_WARPS][4096];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* s = sm[warp];
+    uint8_t* s = sm[warp];
+    const int rho = stage_rho<4>(lane);
     const int64_t ntiles = (n + 1023) / 1024;
     for (int64_t tile = (int64_t)blockIdx.x * CV_WARPS + warp; tile < ntiles;
          tile += (int64_t)gridDim.x * CV_WARPS) {
         uint32_t x[B], r[32];
+        const uint32_t* src = in + tile * 32 + lane;
 #pragma unroll
-        for (int b = 0; b < B; ++b) x[b] = __ldcs(in + b * S + tile * 32 + lane);
+        for (int b = 0; b < B; ++b) x[b] = rotr32(__ldcs(src + b * S), rho);
         to_f32<E, M, mode_ftz(R)>(x, r);
-#pragma unroll
-        for (int b = 0; b < 32; ++b) s[b * CV_ROW + lane] = r[b];
+        transpose32(r);
+        stage_write_column<4>(s, lane, r);
         __syncwarp();
         const int64_t e0 = tile * 1024;
-#pragma unroll 4
-        for (int t = 0; t < 32; ++t) {
-            /* lane b takes slice b of group t; after the transpose lane j
-             * holds element j of the group */
-            const uint32_t v = warp_transpose32(s[lane * CV_ROW + t], lane);
-            const int64_t i = e0 + (int64_t)t * 32 + lane;
-            if (i < n) __stcs(out + i, v);
+        if (vec && e0 + 1024 <= n) {
+            uint4* dst = reinterpret_cast<uint4*>(out + e0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) __stcs(dst + lane + 32 * k, reinterpret_cast<const uint4*>(s)[lane + 32 * k]);
+        } else {
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const int64_t i = e0 + lane + 32 * k;
+                if (i < n) out[i] = reinterpret_cast<const uint32_t*>(s)[lane + 32 * k];
+            }
         }
-        __syncwarp();
+        __syncwarp();   /* the next tile may overwrite the staging area */
     }
 }
 
@@ -114,13 +162,13 @@ struct ConvEntry {
 
 template <int E, int M, int R>
 cudaError_t launch_from_float(const void* in, int src, int64_t n, uint32_t* out, int64_t S, int grid, cudaStream_t s) {
-    from_float_kernel<E, M, R><<<grid, 32 * CV_WARPS, 0, s>>>(in, src, n, out, S);
+    from_float_kernel<E, M, R><<<grid, 32 * CV_WARPS, 0, s>>>(in, src, n, out, S, ((uintptr_t)in & 15u) == 0);
     return cudaGetLastError();
 }
 
 template <int E, int M, int R>
 cudaError_t launch_to_float(const uint32_t* in, int64_t S, int64_t n, uint32_t* out, int grid, cudaStream_t s) {
-    to_float_kernel<E, M, R><<<grid, 32 * CV_WARPS, 0, s>>>(in, S, n, out);
+    to_float_kernel<E, M, R><<<grid, 32 * CV_WARPS, 0, s>>>(in, S, n, out, ((uintptr_t)out & 15u) == 0);
     return cudaGetLastError();
 }
 

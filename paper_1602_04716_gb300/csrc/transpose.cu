@@ -7,105 +7,125 @@
  * container of CB = 1, 2 or 4 bytes (B <= 8, <= 16, <= 32), array index i.
  * Bitslice: bit b of element i is bit (i mod 32) of word b*S + i/32.
  *
- * Both directions are the same 32x32 bit-matrix transpose, done by a warp
- * with one row per lane in five butterfly stages (shfl.xor + funnel rotate +
- * one 3-input merge per stage).  A warp owns a tile of 32 word columns
- * (1024 elements).  For containers narrower than 32 bits one transpose
- * serves 32/(8*CB) element groups at once: lane j's row holds element j of
- * 4/CB consecutive 32-element groups, one per CB-byte lane of the row, and
- * the transposed rows are the planes of those groups side by side.
+ * A warp owns a tile of 32 word columns (1024 elements) and each lane one
+ * column.  Both directions go through the warp's 1024*CB-byte staging area in
+ * shared memory and the in-register transposes of bit_transpose.cuh:
  *
- *  pack:   coalesced container loads -> transpose -> shared memory
- *          [plane][column] -> coalesced 128-byte plane-row stores.
- *  unpack: coalesced 128-byte plane-row loads -> shared memory -> transpose
- *          -> coalesced container stores.
+ *  pack:   coalesced 16-byte loads of the tile -> shared memory -> each lane
+ *          reads its column (32 elements), transposes it in registers and
+ *          stores its B plane words; the warp's stores are 128-byte rows.
+ *  unpack: each lane loads its column's B plane words (128-byte rows per
+ *          warp), transposes them into 32 elements, writes them to shared
+ *          memory -> coalesced 16-byte stores of the tile.
  *
- * Elements past n are packed as zero and every padding word of the planes is
- * written, so a packed operand always has zero padding.
+ * There is no cross-lane shuffle: a column's transpose is 64 (CB = 1), 128
+ * (CB = 2) or 256 (CB = 4) logic instructions of one thread.  Tiles whose
+ * standard array is not 16-byte aligned, and the last, partly filled tile,
+ * move their elements one container at a time instead (coalesced, bounded by
+ * n).  Elements past n are packed as zero and every padding word of the
+ * planes is written, so a packed operand always has zero padding.
  */
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "warp_transpose.cuh"
+#include "bit_transpose.cuh"
 
 namespace bsfp {
 
-constexpr int TP_WARPS = 8;              /* warps per block */
-constexpr int TP_ROW = 33;               /* padded shared-memory row (words) */
+constexpr int TP_WARPS = 8;   /* warps per block */
 
 template <int CB> struct Container;
 template <> struct Container<1> { using T = uint8_t; };
 template <> struct Container<2> { using T = uint16_t; };
 template <> struct Container<4> { using T = uint32_t; };
 
+/* The tile's 1024 containers from the standard array into the staging area:
+ * whole 16-byte chunks when the tile is full and the array 16-byte aligned,
+ * else container by container with zeros past n. */
 template <int CB>
-__global__ void __launch_bounds__(32 * TP_WARPS) pack_kernel(const void* __restrict__ in_, int64_t n, int B,
-                                                             uint32_t* __restrict__ out, int64_t S) {
+__device__ __forceinline__ void stage_load_tile(uint8_t* s, const void* in, int64_t e0, int64_t n, bool vec, int lane) {
     using T = typename Container<CB>::T;
-    constexpr int GP = 4 / CB;           /* element groups per transpose */
-    constexpr int BITS = 8 * CB;
-    __shared__ uint32_t sm[TP_WARPS][32 * TP_ROW];
-    const T* in = static_cast<const T*>(in_);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* s = sm[warp];
-    const int64_t ntiles = S / 32;
-    for (int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * TP_WARPS) {
-        const int64_t e0 = tile * 1024;
-        /* all loads of the tile first, so that they are in flight together */
-        uint32_t rows[32 / GP];
+    if (vec && e0 + 1024 <= n) {
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(in) + e0 * CB);
+        uint4 v[2 * CB];
 #pragma unroll
-        for (int t = 0; t < 32 / GP; ++t) {
-            uint32_t row = 0;
+        for (int k = 0; k < 2 * CB; ++k) v[k] = __ldcs(src + lane + 32 * k);
 #pragma unroll
-            for (int q = 0; q < GP; ++q) {
-                const int64_t i = e0 + (int64_t)(t * GP + q) * 32 + lane;
-                const uint32_t v = (i < n) ? (uint32_t)__ldcs(in + i) : 0u;
-                row |= v << (BITS * q);
-            }
-            rows[t] = row;
+        for (int k = 0; k < 2 * CB; ++k) reinterpret_cast<uint4*>(s)[lane + 32 * k] = v[k];
+    } else {
+        const T* src = static_cast<const T*>(in);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int64_t i = e0 + lane + 32 * k;
+            reinterpret_cast<T*>(s)[lane + 32 * k] = (i < n) ? __ldcs(src + i) : (T)0;
         }
-#pragma unroll
-        for (int t = 0; t < 32 / GP; ++t) {
-            const uint32_t col = warp_transpose32(rows[t], lane);
-            /* lane = BITS*q + b now holds plane b of group t*GP+q */
-            const int b = lane % BITS, g = t * GP + lane / BITS;
-            if (b < B) s[b * TP_ROW + g] = col;
-        }
-        __syncwarp();
-        for (int b = 0; b < B; ++b) out[b * S + tile * 32 + lane] = s[b * TP_ROW + lane];
-        __syncwarp();
     }
 }
 
+/* The staged tile out to the standard array, the first min(1024, n - e0)
+ * containers only. */
 template <int CB>
-__global__ void __launch_bounds__(32 * TP_WARPS) unpack_kernel(const uint32_t* __restrict__ in, int64_t S, int B,
-                                                               void* __restrict__ out_, int64_t n) {
+__device__ __forceinline__ void stage_store_tile(const uint8_t* s, void* out, int64_t e0, int64_t n, bool vec,
+                                                 int lane) {
     using T = typename Container<CB>::T;
-    constexpr int GP = 4 / CB;
-    constexpr int BITS = 8 * CB;
-    constexpr uint32_t VMASK = (CB == 4) ? 0xFFFFFFFFu : ((1u << BITS) - 1u);
-    __shared__ uint32_t sm[TP_WARPS][32 * TP_ROW];
-    T* out = static_cast<T*>(out_);
+    if (vec && e0 + 1024 <= n) {
+        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(out) + e0 * CB);
+#pragma unroll
+        for (int k = 0; k < 2 * CB; ++k) __stcs(dst + lane + 32 * k, reinterpret_cast<const uint4*>(s)[lane + 32 * k]);
+    } else {
+        T* dst = static_cast<T*>(out);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int64_t i = e0 + lane + 32 * k;
+            if (i < n) dst[i] = reinterpret_cast<const T*>(s)[lane + 32 * k];
+        }
+    }
+}
+
+/* The container width of B-bit elements. */
+__host__ __device__ constexpr int container_of(int B) { return B <= 8 ? 1 : (B <= 16 ? 2 : 4); }
+
+template <int B>
+__global__ void __launch_bounds__(32 * TP_WARPS) pack_kernel(const void* __restrict__ in, int64_t n,
+                                                             uint32_t* __restrict__ out, int64_t S, bool vec) {
+    constexpr int CB = container_of(B);
+    __shared__ __align__(16) uint8_t sm[TP_WARPS][1024 * CB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* s = sm[warp];
+    uint8_t* s = sm[warp];
+    const int rho = stage_rho<CB>(lane);
+    const int64_t ntiles = S / 32;
+    for (int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * TP_WARPS) {
+        stage_load_tile<CB>(s, in, tile * 1024, n, vec, lane);
+        __syncwarp();
+        uint32_t w[8 * CB], x[8 * CB];
+        stage_read_column<CB>(s, lane, w);
+        __syncwarp();   /* the next tile may overwrite the staging area */
+        rows_to_planes<CB>(w, x);
+        uint32_t* o = out + tile * 32 + lane;
+#pragma unroll
+        for (int b = 0; b < B; ++b) __stcs(o + b * S, rotl32(x[b], rho));
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(32 * TP_WARPS) unpack_kernel(const uint32_t* __restrict__ in, int64_t S,
+                                                               void* __restrict__ out, int64_t n, bool vec) {
+    constexpr int CB = container_of(B);
+    __shared__ __align__(16) uint8_t sm[TP_WARPS][1024 * CB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t* s = sm[warp];
+    const int rho = stage_rho<CB>(lane);
     const int64_t ntiles = (n + 1023) / 1024;
     for (int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * TP_WARPS) {
-        for (int b = 0; b < B; ++b) s[b * TP_ROW + lane] = __ldcs(in + b * S + tile * 32 + lane);
-        __syncwarp();
-        const int64_t e0 = tile * 1024;
-#pragma unroll 4
-        for (int t = 0; t < 32 / GP; ++t) {
-            const int b = lane % BITS, g = t * GP + lane / BITS;
-            const uint32_t row = (b < B) ? s[b * TP_ROW + g] : 0u;
-            const uint32_t x = warp_transpose32(row, lane);
-            /* lane j: bits BITS*q .. hold element j of group t*GP+q */
+        const uint32_t* src = in + tile * 32 + lane;
+        uint32_t x[8 * CB], w[8 * CB];
 #pragma unroll
-            for (int q = 0; q < GP; ++q) {
-                const int64_t i = e0 + (int64_t)(t * GP + q) * 32 + lane;
-                if (i < n) out[i] = (T)((x >> (BITS * q)) & VMASK);
-            }
-        }
+        for (int b = 0; b < 8 * CB; ++b) x[b] = (b < B) ? rotr32(__ldcs(src + b * S), rho) : 0u;
+        planes_to_rows<CB>(x, w);
+        stage_write_column<CB>(s, lane, w);
         __syncwarp();
+        stage_store_tile<CB>(s, out, tile * 1024, n, vec, lane);
+        __syncwarp();   /* the next tile may overwrite the staging area */
     }
 }
 
@@ -121,33 +141,64 @@ static int num_sms() {
     return g_num_sms;
 }
 
-/* Grid: enough blocks to cover the tiles, at most 8 resident blocks per SM. */
-static int tp_grid(int64_t ntiles) {
+/* Grid: enough blocks to cover the tiles, at most the resident blocks of
+ * every SM (occupancy of the kernel, looked up once). */
+static int tp_grid(const void* kernel, int* occ_cache, int64_t ntiles) {
+    if (*occ_cache <= 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32 * TP_WARPS, 0) != cudaSuccess || occ <= 0) {
+            cudaGetLastError();
+            occ = 4;
+        }
+        *occ_cache = occ;
+    }
     const int64_t want = (ntiles + TP_WARPS - 1) / TP_WARPS;
-    const int64_t cap = (int64_t)num_sms() * 8;
+    const int64_t cap = (int64_t)num_sms() * *occ_cache;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st) {
-    const int grid = tp_grid(S / 32);
-    switch (cb) {
-        case 1: pack_kernel<1><<<grid, 32 * TP_WARPS, 0, st>>>(in, n, B, out, S); break;
-        case 2: pack_kernel<2><<<grid, 32 * TP_WARPS, 0, st>>>(in, n, B, out, S); break;
-        case 4: pack_kernel<4><<<grid, 32 * TP_WARPS, 0, st>>>(in, n, B, out, S); break;
-        default: return cudaErrorInvalidValue;
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+/* One pack and one unpack kernel per plane count B (1..32), the container
+ * width following from B. */
+struct TransposeEntry {
+    const void* pack;
+    const void* unpack;
+    int occ_pack, occ_unpack;   /* resident blocks per SM, looked up once */
+};
+static TransposeEntry g_tp[33];
+
+template <int B>
+static void fill_tp() {
+    g_tp[B] = TransposeEntry{(const void*)pack_kernel<B>, (const void*)unpack_kernel<B>, 0, 0};
+    if constexpr (B < 32) fill_tp<B + 1>();
+}
+
+static const TransposeEntry* tp_entry(int cb, int B) {
+    static bool filled = false;
+    if (!filled) {
+        fill_tp<1>();
+        filled = true;
     }
-    return cudaGetLastError();
+    if (B < 1 || B > 32 || container_of(B) != cb) return nullptr;
+    return &g_tp[B];
+}
+
+cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st) {
+    TransposeEntry* e = const_cast<TransposeEntry*>(tp_entry(cb, B));
+    if (!e) return cudaErrorInvalidValue;
+    bool vec = aligned16(in);
+    void* args[] = {(void*)&in, (void*)&n, (void*)&out, (void*)&S, (void*)&vec};
+    return cudaLaunchKernel(e->pack, dim3(tp_grid(e->pack, &e->occ_pack, S / 32)), dim3(32 * TP_WARPS), args, 0, st);
 }
 
 cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st) {
-    const int grid = tp_grid((n + 1023) / 1024);
-    switch (cb) {
-        case 1: unpack_kernel<1><<<grid, 32 * TP_WARPS, 0, st>>>(in, S, B, out, n); break;
-        case 2: unpack_kernel<2><<<grid, 32 * TP_WARPS, 0, st>>>(in, S, B, out, n); break;
-        case 4: unpack_kernel<4><<<grid, 32 * TP_WARPS, 0, st>>>(in, S, B, out, n); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    TransposeEntry* e = const_cast<TransposeEntry*>(tp_entry(cb, B));
+    if (!e) return cudaErrorInvalidValue;
+    bool vec = aligned16(out);
+    void* args[] = {(void*)&in, (void*)&S, (void*)&out, (void*)&n, (void*)&vec};
+    return cudaLaunchKernel(e->unpack, dim3(tp_grid(e->unpack, &e->occ_unpack, (n + 1023) / 1024)),
+                            dim3(32 * TP_WARPS), args, 0, st);
 }
 
 int device_num_sms() { return num_sms(); }

@@ -89,6 +89,32 @@ def test_to_float_matches_oracle(E, M):
                                                                              want[bad[0]])
 
 
+@pytest.mark.parametrize("E,M", [(5, 7), (4, 3), (8, 23)])
+def test_conversions_of_arrays_not_16_byte_aligned(E, M):
+    """Source and destination float arrays one element past a 16-byte
+    boundary take the element-by-element path of every tile: same results as
+    the oracle, and to_float writes exactly n values."""
+    B = 1 + E + M
+    x = _f32_inputs(3000, 700 + E * 32 + M)
+    n = x.size
+    f = bs.Format(E, M, 0)
+    for src in (bs.FLOAT32, bs.BFLOAT16, bs.FLOAT16):
+        xs = _as_f32_bits(x, src)
+        d = _dev_src(x, src)
+        base = torch.zeros(n + 8, dtype=d.dtype, device="cuda")
+        base[1:n + 1] = d
+        out = torch.full((B * bs.bsfp_plane_stride(n),), -1, dtype=torch.int32, device="cuda")
+        bs.bsfp_from_float(f, base[1:n + 1], n, out)
+        got = out.cpu().numpy().view(np.uint32).reshape(B, -1)
+        assert (got == oracle.pack(B, oracle.from_f32(E, M, 0, xs))).all(), "src=%d" % src
+    planes = torch.from_numpy(oracle.pack(B, synth.fp_values(E, M, n, 9).astype(np.uint32)).view(np.int32).copy()).cuda()
+    guard = torch.full((n + 8,), 7, dtype=torch.int32, device="cuda")
+    bs.bsfp_to_float(f, planes, n, guard[1:n + 1])
+    g = guard.cpu().numpy().view(np.uint32)
+    assert (g[1:n + 1] == oracle.to_f32(E, M, 0, synth.fp_values(E, M, n, 9).astype(np.uint32))).all()
+    assert g[0] == 7 and (g[n + 1:] == 7).all()
+
+
 def test_round_trip_at_scale():
     """2^24 + 5 binary32 values -> 1/5/10 -> binary32 equals numpy's
     binary32 -> binary16 -> binary32 (round to nearest even)."""

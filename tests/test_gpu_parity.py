@@ -111,6 +111,32 @@ def test_pack_unpack_vs_oracle(E, M, n):
     assert (got == x).all(), "unpack(pack(x)) != x"
 
 
+@pytest.mark.parametrize("E,M", [(4, 3), (5, 7), (8, 23), (2, 1), (6, 17)])
+@pytest.mark.parametrize("offset", [1, 3])
+def test_pack_unpack_standard_array_not_16_byte_aligned(E, M, offset):
+    """A standard array aligned only to its container size (here `offset`
+    containers past a 16-byte boundary) takes the element-by-element path of
+    every tile; results equal the oracle's, and unpack writes exactly n
+    containers (the guard containers around the output stay untouched)."""
+    B = 1 + E + M
+    n = 5 * 1024 + 333
+    f = bs.Format(E, M)
+    cb = bs.bsfp_container_bytes(f)
+    cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[cb]
+    raw = synth.uniform_bits(8 * cb, n, 41 + B, dtype=cdt)
+    x = (raw.astype(np.uint64) & ((1 << B) - 1)).astype(np.uint32)
+    base = torch.zeros(n + 16, dtype=bs.container_dtype(f), device="cuda")
+    base[offset:offset + n] = dev(raw)
+    planes = torch.full((B * bs.bsfp_plane_stride(n),), -1, dtype=torch.int32, device="cuda")
+    bs.bsfp_pack(f, base[offset:offset + n], n, planes)
+    assert (host_u32(planes).reshape(B, -1) == oracle.pack(B, x)).all()
+    guard = torch.full((n + 16,), 0x5A, dtype=bs.container_dtype(f), device="cuda")
+    bs.bsfp_unpack(f, planes, n, guard[offset:offset + n])
+    g = guard.cpu().numpy().view(cdt).astype(np.uint32)
+    assert (g[offset:offset + n] == x).all()
+    assert (g[:offset] == 0x5A).all() and (g[offset + n:] == 0x5A).all()
+
+
 def test_unpack_of_oracle_planes():
     E, M, n = 5, 7, 70001
     x = synth.fp_values(E, M, n, 3).astype(np.uint32)
