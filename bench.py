@@ -57,14 +57,22 @@ NCU_TRAFFIC = {(5, 7, "add", 2): (218.124544e6 + 69.806080e6) * 4,
 
 class DeviceTimer:
     """Device time of single calls (CUDA events on the launching stream).
-    Before each timed call a 256 MB buffer is written on the same stream: it
-    evicts the 129 MB L2, so no operand is served from the previous call's
-    cache, and it keeps the GPU busy while the host enqueues the first event
-    and the call, so the host's launch latency is not counted."""
+    Before each timed call the L2 is flushed on the same stream: a 256 MB
+    buffer is written (which evicts the 129 MB L2), then a second 256 MB
+    buffer is read, which writes the first one's dirty lines back to HBM and
+    leaves the L2 holding clean lines only.  So no operand is served from the
+    previous call's cache, the timed call does not pay for write-backs of the
+    flush, and the GPU stays busy while the host enqueues the first event and
+    the call, so the host's launch latency is not counted."""
 
     def __init__(self, torch, stream, flush_bytes: int = 256 << 20):
         self.torch, self.stream = torch, stream
         self.buf = torch.empty(flush_bytes // 4, dtype=torch.int32, device="cuda")
+        self.clean = torch.zeros(flush_bytes // 4, dtype=torch.int32, device="cuda")
+
+    def flush(self):
+        self.buf.fill_(0)
+        self.clean.sum()
 
     def ms(self, fn, reps: int = 5) -> float:
         torch = self.torch
@@ -73,7 +81,7 @@ class DeviceTimer:
         with torch.cuda.stream(self.stream):
             for _ in range(reps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                self.buf.fill_(0)
+                self.flush()
                 e0.record(self.stream)
                 fn()
                 e1.record(self.stream)

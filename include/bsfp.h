@@ -265,7 +265,10 @@ bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t 
  *
  * jobs is host memory read by an asynchronous copy on s: pageable memory is
  * staged before the call returns; page-locked memory must stay unchanged
- * until s has passed the call.  Errors: njobs < 0 or > BSFP_NOALLOC_MAX_JOBS,
+ * until s has passed the call (if it changes in between so that the jobs the
+ * kernels read differ from the ones validated, the persistent kernels skip
+ * all their work and the fault word of bsfp_fault_status becomes 1).  s must
+ * be a stream of the current device.  Errors: njobs < 0 or > BSFP_NOALLOC_MAX_JOBS,
  * or more than BSFP_NOALLOC_MAX_TILES tiles, return BSFP_ERR_SIZE; any
  * invalid job returns its bsfp_add/... error.  All checks come before
  * anything is launched. */
@@ -330,6 +333,16 @@ typedef struct {
     int32_t max_batch_jobs;  /* requests per micro-batch, 1..4096 (0 = 1024) */
     int32_t max_batch_tiles; /* 32,768-element tiles per micro-batch, 128..2^20 (0 = 2^16) */
     int32_t wpt;             /* words per thread of the persistent kernels, 1 or 2 (0 = 2) */
+    /* Admission.  While fewer than eager_slots micro-batches are in flight a
+     * free slot takes the pending requests at once (latency first).  With
+     * eager_slots or more in flight the GPU is already busy, so a free slot
+     * waits until min_batch_tiles tiles are pending or the oldest pending
+     * request has waited batch_wait_us, and then takes everything that fits
+     * (throughput first: fewer, larger micro-batches). */
+    int32_t eager_slots;     /* 1..slots (0 = slots: every free slot admits at once) */
+    int32_t min_batch_tiles; /* 1..2^20 (0 = 2 x the SM count) */
+    int32_t batch_wait_us;   /* 0..10^6 (0 = 20; -1 = admit without waiting) */
+    int32_t reserved;        /* 0 */
 } bsfp_server_options;
 
 /* One finished request.  Times are host steady-clock nanoseconds: submission,
@@ -365,6 +378,14 @@ bsfp_status bsfp_server_create(const bsfp_server_options* opt, bsfp_server* out)
  * whole budget returns BSFP_ERR_BUDGET.  *id_out receives the request id
  * (increasing from 1).  Thread-safe; never blocks on the GPU. */
 bsfp_status bsfp_server_submit(bsfp_server srv, const bsfp_job* job, int64_t* id_out);
+/* Submit n requests at once (the same as n bsfp_server_submit calls in
+ * order, under one lock): every job is validated first; if one fails, its
+ * error is returned, *bad_index (if not NULL) gets its index and no job is
+ * submitted.  ids_out (n entries, may be NULL) receives the ids.  Cheaper
+ * per request than single submissions when requests arrive in bursts.
+ * n == 0 does nothing; n < 0 returns BSFP_ERR_SIZE. */
+bsfp_status bsfp_server_submit_n(bsfp_server srv, const bsfp_job* jobs, int32_t n, int64_t* ids_out,
+                                 int32_t* bad_index);
 /* Move up to max finished requests into done[] (oldest first); returns how
  * many.  Thread-safe. */
 int32_t bsfp_server_poll(bsfp_server srv, bsfp_completion* done, int32_t max);
@@ -438,6 +459,11 @@ bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blo
  * fill).  -1 on a bad argument, 0 if the format is not compiled.  Needs the
  * device only for its SM count. */
 int32_t bsfp_variant_for(bsfp_format f, int32_t op, int64_t n);
+/* Shape of the streamed kernel of (format, op): *tile_words = word columns
+ * per tile (a tile takes one ring stage), *stages = ring stages per block
+ * (one block per SM).  BSFP_ERR_UNSUPPORTED if (format, op) has no streamed
+ * kernel; BSFP_ERR_NULL for a NULL output.  No device is needed. */
+bsfp_status bsfp_stream_shape(bsfp_format f, int32_t op, int32_t* tile_words, int32_t* stages);
 /* Self-test of the streamed kernel's bounded waits: runs (format, op) on a,
  * b -> out (n elements) with the streamed kernel, but issues no copies for
  * tile withhold_tile (0 <= tile < number of tiles; -1 withholds none), and

@@ -67,7 +67,8 @@ class bsfp_batch_options(ctypes.Structure):
 
 class bsfp_server_options(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("max_batch_jobs", ctypes.c_int32),
-                ("max_batch_tiles", ctypes.c_int32), ("wpt", ctypes.c_int32)]
+                ("max_batch_tiles", ctypes.c_int32), ("wpt", ctypes.c_int32), ("eager_slots", ctypes.c_int32),
+                ("min_batch_tiles", ctypes.c_int32), ("batch_wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class bsfp_completion(ctypes.Structure):
@@ -131,6 +132,7 @@ def _lib():
                 "bsfp_launch_count": (i64, []),
                 "bsfp_fault_status": (i32, [i32]),
                 "bsfp_variant_for": (i32, [F, i32, i64]),
+                "bsfp_stream_shape": (i32, [F, i32, ctypes.c_void_p, ctypes.c_void_p]),
                 "bsfp_set_stream_min_tiles": (i32, [i32]),
                 "bsfp_set_batch_stream_min_tiles": (i32, [i32]),
                 "bsfp_stream_selftest": (i32, [F, i32, p, p, p, i64, i64, i64, p]),
@@ -149,6 +151,8 @@ def _lib():
                 "bsfp_pipeline_free": (None, [p]),
                 "bsfp_server_create": (i32, [ctypes.POINTER(bsfp_server_options), ctypes.POINTER(p)]),
                 "bsfp_server_submit": (i32, [p, ctypes.POINTER(bsfp_job), ctypes.POINTER(i64)]),
+                "bsfp_server_submit_n": (i32, [p, ctypes.POINTER(bsfp_job), i32, ctypes.POINTER(i64),
+                                               ctypes.POINTER(i32)]),
                 "bsfp_server_poll": (i32, [p, ctypes.POINTER(bsfp_completion), i32]),
                 "bsfp_server_release": (i32, [p, i64]),
                 "bsfp_server_drain": (i32, [p, i64]),
@@ -329,6 +333,14 @@ def bsfp_variant_for(f, op, n: int) -> int:
     return int(_lib().bsfp_variant_for(_fmt(f), OPS.get(op, op), n))
 
 
+def bsfp_stream_shape(f, op) -> tuple:
+    """(tile words, ring stages) of the streamed kernel of (f, op)."""
+    tw, st = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(_lib().bsfp_stream_shape(_fmt(f), OPS.get(op, op), ctypes.addressof(tw), ctypes.addressof(st)),
+           "bsfp_stream_shape")
+    return tw.value, st.value
+
+
 def bsfp_stream_selftest(f, op, a, b, out, n: int, withhold_tile: int, wait_cycles: int, stream=None):
     """Streamed kernel with one tile's copies withheld and a short wait bound
     (the failure path of its bounded waits)."""
@@ -475,9 +487,10 @@ class Server:
     operands).  Operand tensors must outlive the requests that use them."""
 
     def __init__(self, budget_bytes: int, slots: int = 0, max_batch_jobs: int = 0, max_batch_tiles: int = 0,
-                 wpt: int = 0):
+                 wpt: int = 0, eager_slots: int = 0, min_batch_tiles: int = 0, batch_wait_us: int = 0):
         self._h = ctypes.c_void_p()
-        opt = bsfp_server_options(budget_bytes, slots, max_batch_jobs, max_batch_tiles, wpt)
+        opt = bsfp_server_options(budget_bytes, slots, max_batch_jobs, max_batch_tiles, wpt, eager_slots,
+                                  min_batch_tiles, batch_wait_us, 0)
         _check(_lib().bsfp_server_create(ctypes.byref(opt), ctypes.byref(self._h)), "bsfp_server_create")
 
     def submit(self, f, op, a, b, n: int, c=None, out=None) -> int:
@@ -485,6 +498,13 @@ class Server:
         rid = ctypes.c_int64()
         _check(_lib().bsfp_server_submit(self._h, ctypes.byref(job), ctypes.byref(rid)), "bsfp_server_submit")
         return rid.value
+
+    def submit_n(self, jobs, njobs: int) -> list:
+        """Submit a ctypes array of bsfp_job in one call; returns the ids."""
+        ids = (ctypes.c_int64 * max(1, njobs))()
+        bad = ctypes.c_int32(-1)
+        _check(_lib().bsfp_server_submit_n(self._h, jobs, njobs, ids, ctypes.byref(bad)), "bsfp_server_submit_n")
+        return [ids[i] for i in range(njobs)]
 
     def poll(self, max_items: int = 256) -> list:
         buf = (bsfp_completion * max_items)()

@@ -30,6 +30,19 @@ GEN_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7), (8, 23)]
 # Formats with a streamed kernel (stream.cuh): the generated formats of at
 # most 16 planes.
 STREAM_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
+# The element-wise kernels are compiled in parts: exponent width E and a
+# range of fraction widths.  For every other format of a part, circuitgen
+# prints add and mul under RN and RZ into that part's own header
+# (gen_e<E>_m<lo>.cuh), which only the part's translation unit includes.
+M_RANGES = ((1, 11), (12, 23))
+
+
+def part_formats(e, lo, hi):
+    return [(e, m) for m in range(lo, hi + 1) if 1 + e + m <= 32 and (e, m) not in GEN_FORMATS]
+
+
+def part_header(e, lo):
+    return "gen_e%d_m%d.cuh" % (e, lo)
 
 
 def nvcc() -> str:
@@ -46,9 +59,10 @@ def _units():
           "-DBSFP_HAVE_GEN", "-c"]
     units = []
     for e in range(2, 9):
-        for lo, hi in ((1, 11), (12, 23)):
+        for lo, hi in M_RANGES:
             units.append(("binop_e%d_m%d.o" % (e, lo),
                           cu + ["-DBSFP_E=%d" % e, "-DBSFP_M_LO=%d" % lo, "-DBSFP_M_HI=%d" % hi,
+                                '-DBSFP_GEN_PART="%s"' % part_header(e, lo),
                                 os.path.join(CSRC, "binop_inst.cu")]))
         units.append(("gatecount_e%d.o" % e,
                       ["g++", "-std=c++17", "-O1", "-fPIC", "-I", CSRC, "-DBSFP_E=%d" % e, "-c",
@@ -62,6 +76,7 @@ def _units():
                                                          os.path.join(CSRC, "stream_inst.cu")]))
     for opc in range(3):
         units.append(("batch_opc%d.o" % opc, cu + ["-DBSFP_BATCH_OPC=%d" % opc, os.path.join(CSRC, "batch_inst.cu")]))
+
     for src in ("api.cu", "batch.cu", "batch_noalloc.cu", "serve.cu", "pipeline.cu", "autotune.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):
         units.append((src.replace(".cu", ".o"), cu + [os.path.join(CSRC, src)]))
     return units
@@ -71,27 +86,47 @@ def _deps():
     return glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INC, "*.h"))
 
 
-def generate() -> str:
-    """Compile circuitgen for GEN_FORMATS and print their netlists into
-    _build/gen/gen_circuits.cuh (redone only when a circuit source changed)."""
+def _generate_one(defines, out_path, tag):
+    """Compile circuitgen with the given format lists and print one header."""
+    tool = os.path.join(BUILD, "circuitgen_" + tag)
+    subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", CSRC, *defines, os.path.join(CSRC, "circuitgen.cpp"),
+                           "-o", tool])
+    tmp = out_path + ".tmp"
+    subprocess.check_call([tool, tmp])
+    os.replace(tmp, out_path)
+
+
+def generate(jobs: int | None = None) -> str:
+    """Print the netlists: all ops and modes of GEN_FORMATS into
+    _build/gen/gen_circuits.cuh, and add/mul (RN, RZ) of every other format
+    into its part's header; redone only when a circuit source changed."""
     os.makedirs(GEN_DIR, exist_ok=True)
     srcs = [os.path.join(CSRC, f) for f in ("circuitgen.cpp", "netlist.h", "circuit.cuh")] + [__file__]
-    if os.path.exists(GEN_HEADER) and os.path.getmtime(GEN_HEADER) >= max(os.path.getmtime(p) for p in srcs):
-        return GEN_HEADER
-    tool = os.path.join(BUILD, "circuitgen")
+    newest = max(os.path.getmtime(p) for p in srcs)
+    todo = []
     fmts = " ".join("X(%d, %d)" % fm for fm in GEN_FORMATS)
-    subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", CSRC, "-DBSFP_GEN_FORMATS=" + fmts,
-                           os.path.join(CSRC, "circuitgen.cpp"), "-o", tool])
-    tmp = GEN_HEADER + ".tmp"
-    subprocess.check_call([tool, tmp])
-    os.replace(tmp, GEN_HEADER)
+    todo.append((["-DBSFP_GEN_FORMATS=" + fmts], GEN_HEADER, "tuned"))
+    for e in range(2, 9):
+        for lo, hi in M_RANGES:
+            ys = " ".join("Y(%d, %d)" % fm for fm in part_formats(e, lo, hi))
+            path = os.path.join(GEN_DIR, part_header(e, lo))
+            if ys:
+                todo.append((["-DBSFP_GEN_ADDMUL=" + ys], path, "e%d_m%d" % (e, lo)))
+            elif not os.path.exists(path) or os.path.getmtime(path) < newest:
+                with open(path, "w") as fh:
+                    fh.write("/* no formats of this part need printed netlists */\n")
+    todo = [t for t in todo if not os.path.exists(t[1]) or os.path.getmtime(t[1]) < newest]
+    with ThreadPoolExecutor(jobs or max(1, os.cpu_count() or 1)) as ex:
+        for fut in [ex.submit(_generate_one, *t) for t in todo]:
+            fut.result()
     return GEN_HEADER
 
 
 def build(jobs: int | None = None, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    generate()
-    newest = max(os.path.getmtime(p) for p in _deps() + [GEN_HEADER])
+    generate(jobs)
+    gen = glob.glob(os.path.join(GEN_DIR, "*.cuh"))
+    newest = max(os.path.getmtime(p) for p in _deps() + gen)
     units = _units()
     todo = [(o, c) for o, c in units
             if not os.path.exists(os.path.join(BUILD, o)) or os.path.getmtime(os.path.join(BUILD, o)) < newest]

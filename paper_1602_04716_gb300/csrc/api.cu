@@ -112,12 +112,30 @@ struct Shape {
     int16_t fb_bps;
 };
 
-/* Variant and blocks/SM of a call on S plane words under shape sh (the
- * lock on the shapes held). */
+/* Variant and blocks/SM of a call on S plane words under shape sh. */
 static void pick_shape(const Shape& sh, const BinopEntry* e, int64_t S, int* wpt, int* bps);
-static Shape g_shape[TAB_E][TAB_M][TAB_R][OPC_ALL];
-static int g_occ[TAB_E][TAB_M][TAB_R][OPC_ALL][5];   /* cached occupancy per wpt */
+/* The shapes, each packed into one atomic word: a launch reads its shape
+ * with one load and takes no lock; writers (bsfp_set_variant) serialise on
+ * g_shape_mu for their read-modify-write. */
+static std::atomic<uint64_t> g_shape[TAB_E][TAB_M][TAB_R][OPC_ALL];
+static std::atomic<int> g_occ[TAB_E][TAB_M][TAB_R][OPC_ALL][5];   /* cached occupancy per wpt */
 static std::mutex g_shape_mu;
+
+static uint64_t pack_shape(const Shape& s) {
+    return (uint64_t)(uint8_t)s.wpt | ((uint64_t)(uint16_t)s.bps << 8) | ((uint64_t)(uint8_t)s.fb_wpt << 24) |
+           ((uint64_t)(uint16_t)s.fb_bps << 32);
+}
+static Shape unpack_shape(uint64_t v) {
+    Shape s;
+    s.wpt = (int8_t)(uint8_t)(v & 0xFFu);
+    s.bps = (int16_t)(uint16_t)((v >> 8) & 0xFFFFu);
+    s.fb_wpt = (int8_t)(uint8_t)((v >> 24) & 0xFFu);
+    s.fb_bps = (int16_t)(uint16_t)((v >> 32) & 0xFFFFu);
+    return s;
+}
+static Shape load_shape(const bsfp_format& f, int opc) {
+    return unpack_shape(g_shape[f.exp_bits][f.man_bits][f.rnd][opc].load(std::memory_order_acquire));
+}
 
 static std::atomic<int64_t> g_launches{0};
 static thread_local int32_t g_last_cuda = 0;
@@ -159,14 +177,16 @@ static const BinopEntry* entry_for(const bsfp_format& f, int opc) {
 }
 
 static int occupancy(const bsfp_format& f, int opc, const BinopEntry* e, int wpt) {
-    int& o = g_occ[f.exp_bits][f.man_bits][f.rnd][opc][wpt];
-    if (o == 0) {
-        int blocks = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->kernel(wpt), 128, 0) != cudaSuccess || blocks < 1)
-            blocks = 1;
-        o = blocks;
+    std::atomic<int>& o = g_occ[f.exp_bits][f.man_bits][f.rnd][opc][wpt];
+    int v = o.load(std::memory_order_relaxed);
+    if (v == 0) {   /* looked up once; racing first calls store the same value */
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, e->kernel(wpt), 128, 0) != cudaSuccess || v < 1) {
+            (void)cudaGetLastError();
+            v = 1;
+        }
+        o.store(v, std::memory_order_relaxed);
     }
-    return o;
+    return v;
 }
 
 /* Validate one element-wise op and work out its launch: kernel entry, args,
@@ -180,6 +200,20 @@ static bsfp_status prepare_binop_impl(const bsfp_format& f, int op, const uint32
 bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
                           uint32_t* out, int64_t n, PreparedOp* po) {
     return prepare_binop_impl(f, op, a, b, c, out, n, po, false);
+}
+
+bsfp_status validate_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                           const uint32_t* out, int64_t n, int* opc_out) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    const int opc = opclass(op);
+    if (opc < 0) return BSFP_ERR_UNSUPPORTED;
+    if (n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
+    *opc_out = opc;
+    if (n == 0) return BSFP_OK;
+    if (!a || !b || !out || (opc == OPC_FMA2 && !c)) return BSFP_ERR_NULL;
+    if (!aligned(a, 16) || !aligned(b, 16) || !aligned(out, 16) || (opc == OPC_FMA2 && !aligned(c, 16)))
+        return BSFP_ERR_ALIGN;
+    return entry_for(f, opc) ? BSFP_OK : BSFP_ERR_UNSUPPORTED;
 }
 
 static bsfp_status prepare_binop_impl(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b,
@@ -221,8 +255,7 @@ static bsfp_status prepare_binop_impl(const bsfp_format& f, int op, const uint32
         wpt = VARIANT_STREAMED;
         bps = 1;
     } else {
-        std::lock_guard<std::mutex> lk(g_shape_mu);
-        pick_shape(g_shape[f.exp_bits][f.man_bits][f.rnd][opc], e, p.S, &wpt, &bps);
+        pick_shape(load_shape(f, opc), e, p.S, &wpt, &bps);
         if (wpt != VARIANT_STREAMED) {
             const int occ = occupancy(f, opc, e, wpt);
             bps = (bps > 0 && bps < occ) ? bps : occ;
@@ -277,6 +310,8 @@ bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s) {
 }
 
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int* current_fault_word() { return fault_word(current_device()); }
 
 bsfp_status run_op_by_code(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
                            uint32_t* out, int64_t n, cudaStream_t s) {
@@ -563,9 +598,19 @@ int32_t bsfp_variant_for(bsfp_format f, int32_t op, int64_t n) {
     const BinopEntry* e = entry_for(f, opc);
     if (!e) return 0;
     int wpt, bps;
-    std::lock_guard<std::mutex> lk(g_shape_mu);
-    pick_shape(g_shape[f.exp_bits][f.man_bits][f.rnd][opc], e, bsfp_plane_stride(n), &wpt, &bps);
+    pick_shape(load_shape(f, opc), e, bsfp_plane_stride(n), &wpt, &bps);
     return wpt;
+}
+
+bsfp_status bsfp_stream_shape(bsfp_format f, int32_t op, int32_t* tile_words, int32_t* stages) {
+    if (!format_ok(f)) return BSFP_ERR_FORMAT;
+    if (opclass(op) < 0) return BSFP_ERR_UNSUPPORTED;
+    if (!tile_words || !stages) return BSFP_ERR_NULL;
+    const BinopEntry* e = entry_for(f, opclass(op));
+    if (!e || !(e->wpt_mask & (unsigned)VARIANT_STREAMED)) return BSFP_ERR_UNSUPPORTED;
+    *tile_words = e->stream_tw;
+    *stages = e->stream_nst;
+    return BSFP_OK;
 }
 
 int32_t bsfp_variant(bsfp_format f, int32_t op) {
@@ -573,8 +618,7 @@ int32_t bsfp_variant(bsfp_format f, int32_t op) {
     const int opc = opclass(op);
     const BinopEntry* e = entry_for(f, opc);
     if (!e) return 0;
-    std::lock_guard<std::mutex> lk(g_shape_mu);
-    const Shape sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+    const Shape sh = load_shape(f, opc);
     return (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
 }
 
@@ -586,13 +630,15 @@ bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blo
     const BinopEntry* e = entry_for(f, opc);
     if (!e || (wpt != 0 && !(e->wpt_mask & (unsigned)wpt))) return BSFP_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_shape_mu);
-    Shape& sh = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+    std::atomic<uint64_t>& slot = g_shape[f.exp_bits][f.man_bits][f.rnd][opc];
+    Shape sh = unpack_shape(slot.load(std::memory_order_relaxed));
     sh.wpt = (int8_t)wpt;
     sh.bps = (int16_t)blocks_per_sm;
     if (wpt != VARIANT_STREAMED) {   /* a grid-stride shape (or the default) is also the fallback */
         sh.fb_wpt = (int8_t)wpt;
         sh.fb_bps = (int16_t)blocks_per_sm;
     }
+    slot.store(pack_shape(sh), std::memory_order_release);
     return BSFP_OK;
 }
 

@@ -15,7 +15,8 @@
  *   2. copies the caller's bsfp_job array into the scratch array;
  *   3. launches a one-block prologue kernel that turns the raw jobs into the
  *      descriptors and tile map the persistent kernels read, per op class,
- *      and zeroes the tile counters;
+ *      and zeroes the tile counters (checking its class totals against the
+ *      host's, see noalloc_prologue);
  *   4. launches one persistent kernel per op class present, then a plain
  *      kernel for each job whose format is outside the persistent set.
  *
@@ -55,10 +56,13 @@ constexpr size_t OFF_DESC = OFF_RAW + align256(sizeof(bsfp_job) * BSFP_NOALLOC_M
 constexpr size_t OFF_MAP = OFF_DESC + align256(sizeof(JobDesc) * BSFP_NOALLOC_MAX_JOBS);
 constexpr size_t SCRATCH_BYTES = OFF_MAP + sizeof(int32_t) * (size_t)BSFP_NOALLOC_MAX_TILES;
 
-/* First descriptor and first map entry of each op class (host-computed). */
+/* First descriptor and first map entry of each op class, and each class's
+ * job and tile totals (host-computed from the validated jobs). */
 struct ClassBase {
     int32_t desc0[OPC_COUNT];
     int32_t map0[OPC_COUNT];
+    int32_t njob[OPC_COUNT];
+    int32_t ntile[OPC_COUNT];
 };
 
 __device__ int dev_opclass(int op) {
@@ -117,8 +121,14 @@ __device__ void block_exclusive_scan(int32_t (&v)[V]) {
 
 /* Raw jobs -> per-class descriptors and tile map; counters to zero.  The
  * host has validated every job, so the persistent subset and its tile counts
- * here equal the host's; map writes are still bounded by the scratch size. */
-__global__ void __launch_bounds__(NA_THREADS) noalloc_prologue(unsigned char* scratch, int32_t njobs, ClassBase base) {
+ * here equal the host's -- unless the copied jobs differ from the validated
+ * ones (page-locked jobs changed before the copy ran).  Writes stay inside
+ * the scratch whatever the jobs hold, and at the end the last thread, whose
+ * running counts are then the class totals, compares them with the host's:
+ * on a mismatch it sets every class counter past any tile, so the persistent
+ * kernels take no tile, and raises the fault word. */
+__global__ void __launch_bounds__(NA_THREADS) noalloc_prologue(unsigned char* scratch, int32_t njobs, ClassBase base,
+                                                             int* fault) {
     const bsfp_job* raw = reinterpret_cast<const bsfp_job*>(scratch + OFF_RAW);
     JobDesc* desc = reinterpret_cast<JobDesc*>(scratch + OFF_DESC);
     int32_t* map = reinterpret_cast<int32_t*>(scratch + OFF_MAP);
@@ -138,8 +148,11 @@ __global__ void __launch_bounds__(NA_THREADS) noalloc_prologue(unsigned char* sc
             const int g = dev_opclass(J.op);
             if (g >= 0 && J.n > 0 && dev_kind(J.f.exp_bits, J.f.man_bits, J.f.rnd) >= 0) {
                 const int64_t S = ((J.n + 31) / 32 + 31) / 32 * 32;
+                const int64_t t = (S + NA_TILE - 1) / NA_TILE;
                 cls[k] = g;
-                ntl[k] = (int32_t)((S + NA_TILE - 1) / NA_TILE);
+                /* clamped so that the sums stay in range; more than the
+                 * limit can only come from changed jobs, a mismatch anyway */
+                ntl[k] = (int32_t)(t < BSFP_NOALLOC_MAX_TILES ? t : BSFP_NOALLOC_MAX_TILES + 1);
                 cnt[g] += 1;
                 cnt[OPC_COUNT + g] += ntl[k];
             }
@@ -172,6 +185,16 @@ __global__ void __launch_bounds__(NA_THREADS) noalloc_prologue(unsigned char* sc
         }
         cnt[g] += 1;
         cnt[OPC_COUNT + g] += ntl[k];
+    }
+    if (threadIdx.x == NA_THREADS - 1) {
+        bool same = true;
+#pragma unroll
+        for (int g = 0; g < OPC_COUNT; ++g) same = same && cnt[g] == base.njob[g] && cnt[OPC_COUNT + g] == base.ntile[g];
+        if (!same) {
+#pragma unroll
+            for (int g = 0; g < OPC_COUNT; ++g) counters[g] = 1ull << 62;
+            if (fault) atomicExch(fault, 1);
+        }
     }
 }
 
@@ -271,10 +294,12 @@ extern "C" bsfp_status bsfp_batch_run_noalloc(const bsfp_job* jobs, int32_t njob
         for (int g = 0; g < OPC_COUNT; ++g) {
             base.desc0[g] = d0;
             base.map0[g] = m0;
+            base.njob[g] = njob_c[g];
+            base.ntile[g] = (int32_t)ntile_c[g];
             d0 += njob_c[g];
             m0 += (int32_t)ntile_c[g];
         }
-        noalloc_prologue<<<1, NA_THREADS, 0, st>>>(D->scratch, njobs, base);
+        noalloc_prologue<<<1, NA_THREADS, 0, st>>>(D->scratch, njobs, base, current_fault_word());
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_cuda_error(e);
         launched += 1;

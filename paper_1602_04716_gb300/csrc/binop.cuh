@@ -80,7 +80,9 @@ __device__ __forceinline__ void vstore(uint32_t* p, const uint32_t* w) {
 
 /* The circuit for one word column.  OPC_ADDSUB takes the sign flip at run
  * time (one extra gate) so that add and sub share a kernel.  Formats with a
- * generated netlist (gen_circuit.cuh) run it; the others the templates. */
+ * generated netlist (gen_circuit.cuh) run it -- fma2 as the printed mul then
+ * the printed add where only those two are printed; the others run the
+ * templates. */
 template <int E, int M, int R, int OPC>
 __device__ __forceinline__ void column_op(uint32_t* x, uint32_t* y, const uint32_t* z, uint32_t* r, uint32_t negb) {
     constexpr int B = 1 + E + M;
@@ -88,6 +90,12 @@ __device__ __forceinline__ void column_op(uint32_t* x, uint32_t* y, const uint32
     if constexpr (GenCircuit<E, M, R, OPC>::available) {
         if constexpr (OPC == OPC_ADDSUB) y[B - 1] ^= negb;
         GenCircuit<E, M, R, OPC>::eval(x, y, z, r);
+    } else if constexpr (OPC == OPC_FMA2 && GenCircuit<E, M, R, OPC_MUL>::available &&
+                         GenCircuit<E, M, R, OPC_ADDSUB>::available) {
+        /* the two printed circuits in a row, the rounded product in registers */
+        uint32_t p[B];
+        GenCircuit<E, M, R, OPC_MUL>::eval(x, y, z, p);
+        GenCircuit<E, M, R, OPC_ADDSUB>::eval(p, z, z, r);
     } else if constexpr (OPC == OPC_ADDSUB) {
         y[B - 1] ^= negb;
         fp_add<E, M, RZ, false, FTZ>(x, y, r);
@@ -201,6 +209,7 @@ struct BinopEntry {
     stream_launch_fn stream_launch = nullptr;
     stream_prepare_fn stream_prepare = nullptr;   /* opts in to its shared memory */
     int stream_tw = 0;                            /* words per plane per tile */
+    int stream_nst = 0;                           /* ring stages */
     /* its job-list form, for the batched plans */
     stream_batch_launch_fn stream_batch_launch = nullptr;
     stream_prepare_fn stream_batch_prepare = nullptr;

@@ -16,14 +16,17 @@
  * at G.  This plays the part of the paper's generator (Sec. 5.1: a
  * configuration of formats in, generated code for them out).
  *
- * Usage: circuitgen OUT.cuh    (formats from -DBSFP_GEN_FORMATS="X(E, M) ...")
+ * Usage: circuitgen OUT.cuh    (formats from -DBSFP_GEN_FORMATS="X(E, M) ..."
+ *                               and/or -DBSFP_GEN_ADDMUL="Y(E, M) ...")
  *
- * For each format and rounding mode R (bit 0 toward zero, bit 1 flush to
+ * For each X format and rounding mode R (bit 0 toward zero, bit 1 flush to
  * zero) it prints GenCircuit<E, M, R, OPC>
  * specialisations for the op classes add (b's sign flip is applied by the
  * caller), mul, fma2 and div, with eval(a, b, c, r) over the B slices of each
- * operand.  The printed file is included inside namespace bsfp by
- * gen_circuit.cuh, which defines BSFP_LOP3 and BSFP_GEN_FN.
+ * operand.  For each Y format it prints add and mul under RN and RZ only (the
+ * kernels compose fma2 from those two).  The printed file is included inside
+ * namespace bsfp by gen_circuit.cuh, which defines BSFP_LOP3 and
+ * BSFP_GEN_FN.
  */
 #include <stdio.h>
 
@@ -31,8 +34,14 @@
 
 #include "netlist.h"
 
+#if !defined(BSFP_GEN_FORMATS) && !defined(BSFP_GEN_ADDMUL)
+#error "compile with -DBSFP_GEN_FORMATS=\"X(E, M) ...\" and/or -DBSFP_GEN_ADDMUL=\"Y(E, M) ...\""
+#endif
 #ifndef BSFP_GEN_FORMATS
-#error "compile with -DBSFP_GEN_FORMATS=\"X(E, M) X(E, M) ...\""
+#define BSFP_GEN_FORMATS
+#endif
+#ifndef BSFP_GEN_ADDMUL
+#define BSFP_GEN_ADDMUL
 #endif
 
 namespace bsfp {
@@ -108,6 +117,15 @@ void emit_format(FILE* f) {
     emit_mode<E, M, 3>(f);
 }
 
+/* add and mul, RN and RZ */
+template <int E, int M>
+void emit_addmul(FILE* f) {
+    emit<E, M, 0, OP_ADD>(f, 0);
+    emit<E, M, 0, OP_MUL>(f, 1);
+    emit<E, M, 1, OP_ADD>(f, 0);
+    emit<E, M, 1, OP_MUL>(f, 1);
+}
+
 }  // namespace
 }  // namespace gc
 }  // namespace bsfp
@@ -127,6 +145,9 @@ int main(int argc, char** argv) {
 #define X(E, M) bsfp::gc::emit_format<E, M>(f);
     BSFP_GEN_FORMATS
 #undef X
+#define Y(E, M) bsfp::gc::emit_addmul<E, M>(f);
+    BSFP_GEN_ADDMUL
+#undef Y
     if (fclose(f) != 0) {
         perror(argv[1]);
         return 1;

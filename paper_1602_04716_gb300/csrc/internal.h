@@ -38,8 +38,16 @@ int opclass(int op);
 int device_num_sms();
 bsfp_status prepare_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
                           uint32_t* out, int64_t n, PreparedOp* po);
+/* The argument checks of prepare_binop alone (no launch shape, no device
+ * query, no lock): the same status for the same arguments; *opc_out gets
+ * the op class when the format and op are valid. */
+bsfp_status validate_binop(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,
+                           const uint32_t* out, int64_t n, int* opc_out);
 bsfp_status launch_prepared(const PreparedOp& po, cudaStream_t s);
 void count_launches(int64_t k);
+/* Device address of the fault word of the current device (bsfp_fault_status),
+ * or NULL if it cannot be looked up. */
+int* current_fault_word();
 bsfp_status set_cuda_error(cudaError_t e);
 /* Launch op (bsfp_op code) on stream s through the public entry points. */
 bsfp_status run_op_by_code(const bsfp_format& f, int op, const uint32_t* a, const uint32_t* b, const uint32_t* c,

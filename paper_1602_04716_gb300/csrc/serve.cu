@@ -4,10 +4,14 @@
  * trace replay (bsfp_bench.h).
  *
  * Structure.  Client threads submit requests into a FIFO under the server's
- * mutex.  One worker thread loops: it retires finished micro-batches (a CUDA
- * event per slot), then, for every free slot, admits requests from the head
- * of the FIFO while the slot's descriptor capacity and the result arena
- * allow, and launches them as one micro-batch on the slot's stream: one
+ * mutex (one at a time, or in bursts with bsfp_server_submit_n, which takes
+ * the lock once).  One worker thread loops: it retires finished micro-batches
+ * (a CUDA event per slot), then, for every free slot, admits requests from
+ * the head of the FIFO while the slot's descriptor capacity and the result
+ * arena allow -- at once while few micro-batches are in flight, otherwise
+ * only once enough tiles are pending or the oldest request has waited a
+ * tick, so that a busy GPU gets fewer, larger micro-batches -- and launches
+ * them as one micro-batch on the slot's stream: one
  * host-to-device copy of the descriptors, the tile map and zeroed tile
  * counters from the slot's page-locked staging buffer, then one persistent
  * batched kernel per op class present (the kernels of batch.cuh), then a
@@ -110,6 +114,7 @@ struct Request {
     int64_t S, tiles;
     int64_t t_submit, t_admit, t_done;
     int32_t status;
+    bool polled;         /* handed out by bsfp_server_poll */
 };
 
 struct Slot {
@@ -136,6 +141,7 @@ struct bsfp_server_st {
     std::condition_variable cv_work;   /* worker: new submissions / stop */
     std::condition_variable cv_idle;   /* drain: pending and in-flight changed */
     std::deque<int64_t> pending;
+    int64_t pending_tiles = 0;         /* tiles of the pending requests */
     std::unordered_map<int64_t, Request> reqs;
     std::deque<int64_t> finished;      /* completed, not yet polled */
     int64_t next_id = 1;
@@ -148,6 +154,8 @@ struct bsfp_server_st {
     void run();
     void retire_locked(Slot& s, bool ok, cudaError_t err);
     bool admit_locked(Slot& s);
+    bool may_admit_locked(int64_t now) const;
+    bsfp_status make_request(const bsfp_job& job, Request* r) const;
 };
 
 namespace {
@@ -211,6 +219,7 @@ bool bsfp_server_st::admit_locked(Slot& s) {
             r.kind = -1;
         }
         take.push_back(r.id);
+        pending_tiles -= r.tiles;
         pending.pop_front();
     }
     if (take.empty()) return false;
@@ -299,6 +308,40 @@ bool bsfp_server_st::admit_locked(Slot& s) {
     return true;
 }
 
+/* Validate one job (as the single ops do, without their launch shape) and
+ * fill in what admission needs; no lock is taken. */
+bsfp_status bsfp_server_st::make_request(const bsfp_job& job, Request* r) const {
+    memset(r, 0, sizeof *r);
+    r->job = job;
+    r->own_out = job.out == nullptr;
+    /* an arena result stands in as an aligned placeholder until admission */
+    const uint32_t* out_check = r->own_out ? reinterpret_cast<const uint32_t*>((uintptr_t)ARENA_ALIGN) : job.out;
+    int opc = -1;
+    const bsfp_status v = validate_binop(job.f, job.op, job.a, job.b, job.c, out_check, job.n, &opc);
+    if (v != BSFP_OK) return v;
+    r->S = bsfp_plane_stride(job.n);
+    r->out_bytes = round_up((int64_t)(1 + job.f.exp_bits + job.f.man_bits) * r->S * 4, ARENA_ALIGN);
+    if (r->own_out && r->out_bytes > opt.budget_bytes) return BSFP_ERR_BUDGET;
+    r->opc = opc;
+    r->kind = (job.n == 0 || opc >= OPC_COUNT) ? -1 : batch_kind(job.f.exp_bits, job.f.man_bits, job.f.rnd);
+    const int64_t tile = 128LL * opt.wpt * BATCH_ROUNDS;
+    r->tiles = (r->S + tile - 1) / tile;
+    r->status = BSFP_OK;
+    return BSFP_OK;
+}
+
+/* Admission policy (bsfp_server_options): a free slot takes the pending
+ * requests at once while fewer than eager_slots micro-batches are in flight;
+ * beyond that, only when min_batch_tiles tiles are pending or the head has
+ * waited batch_wait_us. */
+bool bsfp_server_st::may_admit_locked(int64_t now) const {
+    if (pending.empty()) return false;
+    if (inflight < opt.eager_slots || opt.batch_wait_us < 0) return true;
+    if (pending_tiles >= opt.min_batch_tiles) return true;
+    const auto it = reqs.find(pending.front());
+    return it == reqs.end() || now - it->second.t_submit >= (int64_t)opt.batch_wait_us * 1000;
+}
+
 void bsfp_server_st::run() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
@@ -316,6 +359,7 @@ void bsfp_server_st::run() {
         if (!stop) {
             for (Slot& s : slots) {
                 if (s.busy || pending.empty()) continue;
+                if (!may_admit_locked(now_ns())) break;   /* let the batch grow; poll again */
                 if (!admit_locked(s)) {
                     blocked = true;
                     break;
@@ -346,14 +390,20 @@ extern "C" {
 bsfp_status bsfp_server_create(const bsfp_server_options* opt, bsfp_server* out) {
     if (!out) return BSFP_ERR_NULL;
     *out = nullptr;
-    bsfp_server_options o = {1LL << 30, 4, 1024, 1 << 16, 2};
+    bsfp_server_options o;
+    memset(&o, 0, sizeof o);
+    o.budget_bytes = 1LL << 30;
     if (opt) o = *opt;
     if (o.slots == 0) o.slots = 4;
     if (o.max_batch_jobs == 0) o.max_batch_jobs = 1024;
     if (o.max_batch_tiles == 0) o.max_batch_tiles = 1 << 16;
     if (o.wpt == 0) o.wpt = 2;
+    if (o.eager_slots == 0) o.eager_slots = o.slots;
+    if (o.batch_wait_us == 0) o.batch_wait_us = 20;
     if (o.budget_bytes <= 0 || o.slots < 1 || o.slots > 16 || o.max_batch_jobs < 1 || o.max_batch_jobs > 4096 ||
-        o.max_batch_tiles < 128 || o.max_batch_tiles > (1 << 20) || (o.wpt != 1 && o.wpt != 2))
+        o.max_batch_tiles < 128 || o.max_batch_tiles > (1 << 20) || (o.wpt != 1 && o.wpt != 2) ||
+        o.eager_slots < 1 || o.eager_slots > o.slots || o.min_batch_tiles < 0 || o.min_batch_tiles > (1 << 20) ||
+        o.batch_wait_us < -1 || o.batch_wait_us > 1000000 || o.reserved != 0)
         return BSFP_ERR_SIZE;
 
     bsfp_server_st* S = new bsfp_server_st();
@@ -376,6 +426,7 @@ bsfp_status bsfp_server_create(const bsfp_server_options* opt, bsfp_server* out)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(g, o.wpt), 128, 0);
         S->grid_cap[g] = device_num_sms() * (occ > 0 ? occ : 1);
     }
+    if (S->opt.min_batch_tiles == 0) S->opt.min_batch_tiles = 2 * device_num_sms();
     if (err != cudaSuccess) {
         destroy_resources(S);
         delete S;
@@ -388,34 +439,37 @@ bsfp_status bsfp_server_create(const bsfp_server_options* opt, bsfp_server* out)
 
 bsfp_status bsfp_server_submit(bsfp_server S, const bsfp_job* job, int64_t* id_out) {
     if (!S || !job) return BSFP_ERR_NULL;
-    Request r;
-    memset(&r, 0, sizeof r);
-    r.job = *job;
-    r.own_out = job->out == nullptr;
-    /* validate as the single ops do; an arena result stands in as an aligned
-     * placeholder until admission */
-    PreparedOp po;
-    uint32_t* out_check = r.own_out ? reinterpret_cast<uint32_t*>((uintptr_t)ARENA_ALIGN) : job->out;
-    const bsfp_status v = prepare_binop(job->f, job->op, job->a, job->b, job->c, out_check, job->n, &po);
-    if (v != BSFP_OK) return v;
-    r.S = bsfp_plane_stride(job->n);
-    r.out_bytes = round_up((int64_t)(1 + job->f.exp_bits + job->f.man_bits) * r.S * 4, ARENA_ALIGN);
-    if (r.own_out && r.out_bytes > S->opt.budget_bytes) return BSFP_ERR_BUDGET;
-    r.opc = po.skip ? opclass(job->op) : po.opc;
-    r.kind = (po.skip || r.opc >= OPC_COUNT) ? -1 : batch_kind(job->f.exp_bits, job->f.man_bits, job->f.rnd);
-    const int64_t tile = 128LL * S->opt.wpt * BATCH_ROUNDS;
-    r.tiles = (r.S + tile - 1) / tile;
-    r.status = BSFP_OK;
+    return bsfp_server_submit_n(S, job, 1, id_out, nullptr);
+}
+
+bsfp_status bsfp_server_submit_n(bsfp_server S, const bsfp_job* jobs, int32_t n, int64_t* ids_out,
+                                 int32_t* bad_index) {
+    if (!S || (n > 0 && !jobs)) return BSFP_ERR_NULL;
+    if (n < 0) return BSFP_ERR_SIZE;
+    if (n == 0) return BSFP_OK;
+    std::vector<Request> rs((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        const bsfp_status v = S->make_request(jobs[i], &rs[(size_t)i]);
+        if (v != BSFP_OK) {
+            if (bad_index) *bad_index = i;
+            return v;
+        }
+    }
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stop) return BSFP_ERR_UNSUPPORTED;
-        r.id = S->next_id++;
-        r.t_submit = now_ns();
-        S->reqs.emplace(r.id, r);
-        S->pending.push_back(r.id);
-        S->submitted += 1;
+        const int64_t t = now_ns();
+        for (int32_t i = 0; i < n; ++i) {
+            Request& r = rs[(size_t)i];
+            r.id = S->next_id++;
+            r.t_submit = t;
+            S->pending.push_back(r.id);
+            S->pending_tiles += r.tiles;
+            if (ids_out) ids_out[i] = r.id;
+            S->reqs.emplace(r.id, r);
+        }
+        S->submitted += n;
         S->wake_gen += 1;
-        if (id_out) *id_out = r.id;
     }
     S->cv_work.notify_one();
     return BSFP_OK;
@@ -428,7 +482,8 @@ int32_t bsfp_server_poll(bsfp_server S, bsfp_completion* done, int32_t max) {
     while (k < max && !S->finished.empty()) {
         const int64_t id = S->finished.front();
         S->finished.pop_front();
-        const Request& r = S->reqs[id];
+        Request& r = S->reqs[id];
+        r.polled = true;
         bsfp_completion& c = done[k++];
         c.id = id;
         c.status = r.status;
@@ -447,9 +502,7 @@ bsfp_status bsfp_server_release(bsfp_server S, int64_t id) {
     if (!S) return BSFP_ERR_NULL;
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->reqs.find(id);
-    if (it == S->reqs.end() || it->second.t_done == 0) return BSFP_ERR_SIZE;
-    for (int64_t f : S->finished)
-        if (f == id) return BSFP_ERR_SIZE;   /* not polled yet */
+    if (it == S->reqs.end() || it->second.t_done == 0 || !it->second.polled) return BSFP_ERR_SIZE;
     if (it->second.own_out && it->second.out_bytes > 0) S->arena.release(it->second.out_off, it->second.out_bytes);
     S->reqs.erase(it);
     S->wake_gen += 1;
@@ -520,15 +573,21 @@ bsfp_status bsfp_server_replay(bsfp_server S, const bsfp_job* jobs, const int64_
         }
         return k;
     };
-    for (int32_t i = 0; i < n; ++i) {
-        const int64_t due = t0 + arrival_ns[i];
-        while (now_ns() < due) {
+    std::vector<int64_t> ids;
+    for (int32_t i = 0; i < n;) {
+        /* every request whose arrival time has come, in one submission */
+        const int64_t now = now_ns();
+        int32_t j = i;
+        while (j < n && t0 + arrival_ns[j] <= now) ++j;
+        if (j == i) {
             if (collect() == 0) std::this_thread::yield();
+            continue;
         }
-        int64_t id = 0;
-        const bsfp_status st = bsfp_server_submit(S, &jobs[i], &id);
+        ids.resize((size_t)(j - i));
+        const bsfp_status st = bsfp_server_submit_n(S, jobs + i, j - i, ids.data(), nullptr);
         if (st != BSFP_OK) return st;
-        index[id] = i;
+        for (int32_t k = i; k < j; ++k) index[ids[(size_t)(k - i)]] = k;
+        i = j;
     }
     while (got < n) {
         if (collect() == 0) {

@@ -23,9 +23,9 @@
  * doing, and the consumers never wait on global memory.  Tiles go to blocks
  * round-robin (tile t to block t mod gridDim).  Shapes (consumer warps x
  * stages) are fixed per plane count B and op class so that the registers of
- * NC+1 warps and the ring fit one SM: 16 x 3 for B <= 9, 15 x 2 for B = 13,
- * 12 x 2 for B = 16 and 14 x 2 for mul 1/8/7 (measured against neighbouring
- * shapes on 2^28-element operands).
+ * NC+1 warps and the ring fit one SM: 11 x 4 for B <= 9, 11 x 3 (add) and
+ * 15 x 2 (mul) for B = 13, 12 x 2 for B = 16 and 14 x 2 for mul 1/8/7
+ * (measured against neighbouring shapes on 2^28-element operands).
  *
  * Waits are bounded (tma.cuh); a block whose wait gives up stops, lets its
  * copies in flight land, and sets *p.fault, which bsfp_fault_status reports.
@@ -50,12 +50,15 @@ template <int E, int M, int OPC>
 struct StreamShape {
     static constexpr int B = 1 + E + M;
     static constexpr int WPT = 2;                                   /* words per consumer thread */
-    /* consumer warps: 16 x 3 stages for B <= 9, 15 x 2 for B = 13, 12 x 2
-     * for B = 16 -- except mul 1/8/7, 14 x 2 (measured: 14 warps feed its
-     * logic pipe better; 1/5/10 mul gained nothing and its job-list form
+    /* consumer warps x ring stages, each the fastest of its neighbours on
+     * 2^28-element operands: 11 x 4 for B <= 9; for B = 13, 11 x 3 for the
+     * adder (deeper ring, and its light circuit needs fewer warps) and 15 x 2
+     * for mul (more warps feed its logic pipe); 12 x 2 for B = 16, except
+     * mul 1/8/7 at 14 x 2 (1/5/10 mul gained nothing and its job-list form
      * spills there, and the adders stream at the copy bandwidth with 12) */
-    static constexpr int NC = B <= 9 ? 16 : (B <= 13 ? 15 : ((OPC == OPC_MUL && E == 8) ? 14 : 12));
-    static constexpr int NST = B <= 9 ? 3 : 2;                      /* ring stages */
+    static constexpr int NC = B <= 9 ? 11
+                            : (B <= 13 ? (OPC == OPC_ADDSUB ? 11 : 15) : ((OPC == OPC_MUL && E == 8) ? 14 : 12));
+    static constexpr int NST = B <= 9 ? 4 : ((B <= 13 && OPC == OPC_ADDSUB) ? 3 : 2);   /* ring stages */
     static constexpr int NIN = 2 * B;                               /* input planes per tile */
     static constexpr int TW = 32 * NC * WPT;                        /* words per plane per tile */
     static constexpr int THREADS = 32 * (NC + 1);

@@ -20,6 +20,7 @@ static void add_stream(BinopEntry& e) {
     e.stream_launch = stream_launch<E, M, R, OPC>;
     e.stream_prepare = stream_prepare<E, M, R, OPC>;
     e.stream_tw = StreamShape<E, M, OPC>::TW;
+    e.stream_nst = StreamShape<E, M, OPC>::NST;
     e.stream_batch_launch = stream_batch_launch<E, M, R, OPC>;
     e.stream_batch_prepare = stream_batch_prepare<E, M, R, OPC>;
     e.wpt_mask |= (unsigned)VARIANT_STREAMED;

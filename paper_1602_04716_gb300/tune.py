@@ -56,19 +56,23 @@ def apply(path: str = CACHE) -> int:
     return n
 
 
-def time_op(op, f, a, b, c, out, n, reps=5) -> float:
-    """Median milliseconds of one launch."""
+def time_op(op, f, a, b, c, out, n, reps=5, per=3) -> float:
+    """Median milliseconds of one launch, each sample `per` launches in a
+    row between two events (so the host's launch latency overlaps the
+    previous launch instead of being counted)."""
     import torch
     s = torch.cuda.current_stream()
+    _b.bsfp_op(op, f, a, b, out, n, c=c)
     ts = []
-    for _ in range(reps + 1):
+    for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        _b.bsfp_op(op, f, a, b, out, n, c=c)
+        for _ in range(per):
+            _b.bsfp_op(op, f, a, b, out, n, c=c)
         e1.record(s)
         e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    ts = sorted(ts[1:])
+        ts.append(e0.elapsed_time(e1) / per)
+    ts = sorted(ts)
     return ts[len(ts) // 2]
 
 

@@ -288,3 +288,35 @@ def test_tuning_cache_matches_the_build():
         want = {"%d/%d/%d/%s" % (E, M, r, op) for E, M in build.GEN_FORMATS for r in range(4)
                 for op in ("add", "mul", "fma2", "div")}
         assert want <= set(keys), (gpu, sorted(want - set(keys))[:8])
+
+
+def test_stream_shape_query():
+    """Tiles and ring stages of the streamed kernels, as compiled (no device
+    needed); formats and op classes without one are refused."""
+    assert bs.bsfp_stream_shape(bs.Format(5, 7), "add") == (32 * 11 * 2, 3)
+    assert bs.bsfp_stream_shape(bs.Format(5, 7), "sub") == (32 * 11 * 2, 3)
+    assert bs.bsfp_stream_shape(bs.Format(5, 7), "mul") == (32 * 15 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(4, 4, bs.RZ), "mul") == (32 * 11 * 2, 4)
+    assert bs.bsfp_stream_shape(bs.Format(8, 7), "mul") == (32 * 14 * 2, 2)
+    for f, op in ((bs.Format(5, 7), "fma2"), (bs.Format(5, 7), "div"), (bs.Format(3, 5), "add"),
+                  (bs.Format(8, 23), "mul")):
+        with pytest.raises(bs.BsfpError) as ei:
+            bs.bsfp_stream_shape(f, op)
+        assert ei.value.status == bs.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("field,value", [("slots", 17), ("eager_slots", 5), ("eager_slots", -1),
+                                         ("min_batch_tiles", -2), ("batch_wait_us", -2),
+                                         ("batch_wait_us", 2000000), ("reserved", 1), ("wpt", 3)])
+def test_server_options_are_checked_before_anything_is_allocated(field, value):
+    L = _binding._lib()
+    opt = _binding.bsfp_server_options(1 << 20, 4, 0, 0, 0, 0, 0, 0, 0)
+    setattr(opt, field, value)
+    h = ctypes.c_void_p()
+    assert L.bsfp_server_create(ctypes.byref(opt), ctypes.byref(h)) == bs.ERR_SIZE
+    assert not h.value
+
+
+def test_server_bulk_submit_arguments():
+    L = _binding._lib()
+    assert L.bsfp_server_submit_n(None, None, 1, None, None) == bs.ERR_NULL

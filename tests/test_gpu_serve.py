@@ -163,3 +163,43 @@ def test_allocation_failure_is_reported_and_leaves_nothing_behind():
     assert abs(free1 - free0) < (64 << 20)
     srv = bs.Server(1 << 20)      # still works afterwards
     srv.close()
+
+
+def test_burst_submission_is_batched_and_exact():
+    """A burst submitted in one call (bsfp_server_submit_n) is admitted many
+    requests at a time -- a handful of micro-batches for 400 requests -- and
+    every result equals the op run alone."""
+    reqs = _requests(400, 4711, lo=1 << 10, hi=1 << 16)
+    arr, nj = _jobs(reqs)
+    srv = bs.Server(1 << 30, slots=4)
+    ids = srv.submit_n(arr, nj)
+    assert ids == sorted(ids) and len(set(ids)) == nj
+    srv.drain(30000)
+    st = srv.stats()
+    assert st["completed"] == nj and st["failed"] == 0
+    assert st["batches"] <= nj // 20, st
+    got = {}
+    while len(got) < nj:
+        for c in srv.poll():
+            assert c.status == 0
+            got[c.id] = c
+    for k, rid in enumerate(ids):
+        q = reqs[k]
+        c = got[rid]
+        if q["n"]:
+            assert torch.equal(bs.Server.result(c, q["f"]).clone(), _alone(q).flatten()), "request %d" % k
+        srv.release(rid)
+    assert srv.stats()["arena_bytes_in_use"] == 0
+    srv.close()
+
+
+def test_burst_with_an_invalid_job_submits_nothing():
+    reqs = _requests(8, 5150, lo=64, hi=4096, fmts=bs.BATCH_FORMATS)
+    arr, nj = _jobs(reqs)
+    arr[5].a = (arr[5].a or 0) + 4   # misaligned operand
+    srv = bs.Server(1 << 26)
+    with pytest.raises(bs.BsfpError) as ei:
+        srv.submit_n(arr, nj)
+    assert ei.value.status == bs.ERR_ALIGN
+    assert srv.stats()["submitted"] == 0
+    srv.close()

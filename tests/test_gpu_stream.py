@@ -30,9 +30,7 @@ OPS = ["add", "sub", "mul"]
 
 def shape(E, M, op="add"):
     """(tile words per plane, ring stages) of the streamed kernel."""
-    B = 1 + E + M
-    nc = 16 if B <= 9 else (15 if B <= 13 else (14 if (op == "mul" and E == 8) else 12))
-    return 32 * nc * 2, (3 if B <= 9 else 2)
+    return bs.bsfp_stream_shape(bs.Format(E, M), op)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -102,7 +100,8 @@ def test_several_rounds_of_the_ring(E, M):
     word of the output planes, and 4,096 sampled elements plus the tail agree
     with the oracle, in all four modes."""
     B = 1 + E + M
-    TW, NST = shape(E, M, "add")   # the smaller tile: every op class gets NST + 2 tiles per block or more
+    # every op class gets NST + 2 tiles per block or more
+    TW, NST = max((shape(E, M, op) for op in ("add", "mul")), key=lambda s: s[0] * (s[1] + 2))
     n = bs.bsfp_num_sms() * (NST + 2) * 32 * TW - 3 * 32 * TW // 2 + 12345
     cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[bs.bsfp_container_bytes(bs.Format(E, M))]
     std = bs.empty_standard(bs.Format(E, M), n)
@@ -172,7 +171,7 @@ def test_small_calls_fall_back_to_the_grid_stride_kernel():
     the ring runs the default grid-stride variant; results do not change."""
     E, M = 5, 7
     f = bs.Format(E, M)
-    TW, _ = shape(E, M)
+    TW, _ = shape(E, M, "mul")
     sms = bs.bsfp_num_sms()
     bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED)
     try:
@@ -195,7 +194,7 @@ def test_bounded_wait_runs_out_and_reports():
     E, M = 5, 7
     B = 1 + E + M
     f = bs.Format(E, M)
-    TW, NST = shape(E, M)
+    TW, NST = shape(E, M, "mul")
     n = bs.bsfp_num_sms() * (NST + 2) * 32 * TW
     a = torch.zeros(B * bs.bsfp_plane_stride(n), dtype=torch.int32, device="cuda")
     b = torch.zeros_like(a)
@@ -232,7 +231,7 @@ def test_in_place_output(op):
     E, M = 5, 7
     B = 1 + E + M
     f = bs.Format(E, M)
-    TW, NST = shape(E, M)
+    TW, NST = shape(E, M, op)
     n = bs.bsfp_num_sms() * (NST + 1) * 32 * TW + 999
     a = synth.fp_values(E, M, n, 61).astype(np.uint32)
     b = synth.fp_values(E, M, n, 62).astype(np.uint32)
