@@ -506,8 +506,9 @@ def batched_workload(bs, torch, njobs, lo, hi, seed, rank=0, formats=BATCH_FORMA
 
 
 def run_batched(bs, torch, args, rank, hbm):
-    """Batched plans -- the persistent kernels (one per op class) and the
-    streamed kernels (one per format and op class) -- vs per-vector plain
+    """Batched plans -- the persistent kernels (one per op class), the
+    streamed kernels (one per format and op class) and the unified streamed
+    kernels (one per op class, every format) -- vs per-vector plain
     launches, in a graph and without, on one mixed workload (4,096 vectors,
     lengths log-uniform in [1,024, 4,194,304], formats uniform over the five
     batched formats, add/mul 50/50).  The speedups are those of the faster
@@ -538,18 +539,21 @@ def run_batched(bs, torch, args, rank, hbm):
     variants["persistent_graph"] = timed(lambda: persistent.run(stream), args.batch_steps)
     streamed = bs.BatchPlan(arr, nj, bs.BATCH_STREAMED, wpt, bps)   # its persistent part takes the tuned shape
     variants["streamed_graph"] = timed(lambda: streamed.run(stream), args.batch_steps)
+    unified = bs.BatchPlan(arr, nj, bs.BATCH_UNIFIED, wpt, bps)
+    variants["unified_graph"] = timed(lambda: unified.run(stream), args.batch_steps)
     plain_graph = bs.BatchPlan(arr, nj, bs.BATCH_PLAIN)
     variants["plain_graph"] = timed(lambda: plain_graph.run(stream), args.batch_steps)
     variants["plain_launches"] = timed(lambda: bs.bsfp_launch_jobs(arr, nj, stream), args.batch_steps)
     for k, (ms, launches) in variants.items():
         res[k] = {"ms_per_step": ms, "elements_per_s": elems / (ms * 1e-3), "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
                   "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "launches_per_step": launches}
-    best = min(("persistent_graph", "streamed_graph"), key=lambda k: variants[k][0])
+    best = min(("persistent_graph", "streamed_graph", "unified_graph"), key=lambda k: variants[k][0])
     res["best_batched"] = best
     res["speedup_vs_plain_graph"] = variants["plain_graph"][0] / variants[best][0]
     res["speedup_vs_plain_launches"] = variants["plain_launches"][0] / variants[best][0]
     persistent.free()
     streamed.free()
+    unified.free()
     plain_graph.free()
     del keep
     return res

@@ -187,9 +187,12 @@ typedef struct bsfp_batch_plan_st* bsfp_batch_plan;
 typedef enum {
     BSFP_BATCH_PERSISTENT = 0, /* one persistent kernel per op class over all tiles */
     BSFP_BATCH_PLAIN = 1,      /* one plain kernel launch per job, captured in the graph */
-    BSFP_BATCH_STREAMED = 2    /* one streamed kernel (BSFP_VARIANT_STREAMED, in its job-list
+    BSFP_BATCH_STREAMED = 2,   /* one streamed kernel (BSFP_VARIANT_STREAMED, in its job-list
                                   form) per format, rounding and op class that has one, over the
                                   tiles of all its jobs; the remaining jobs as in PERSISTENT */
+    BSFP_BATCH_UNIFIED = 3     /* the RN/RZ add/sub and mul jobs of the persistent formats in one
+                                  streamed kernel per op class whatever their format (tiles from
+                                  an atomic counter); the remaining jobs as in STREAMED */
 } bsfp_batch_mode;
 
 /* Launch shape of a plan.  wpt: words per thread in the persistent kernels
@@ -212,7 +215,11 @@ typedef struct {
  * all its jobs round-robin.  The RN/RZ groups do so when they hold at least
  * 8 tiles per SM on average (bsfp_set_batch_stream_min_tiles); otherwise
  * they all stay with the persistent kernels.  Flush-to-zero groups, which
- * the persistent kernels do not cover, always stream.  The plan owns a device buffer (job descriptors, the tile-to-
+ * the persistent kernels do not cover, always stream.  In BSFP_BATCH_UNIFIED
+ * mode the RN/RZ add/sub jobs of those five formats go to one streamed
+ * kernel and their mul jobs to another, each a single launch that streams
+ * the tiles of every format through one shared-memory ring, taking tiles
+ * from an atomic counter; the other jobs go as in BSFP_BATCH_STREAMED.  The plan owns a device buffer (job descriptors, the tile-to-
  * job map and the counters, allocated here) and a CUDA graph capturing
  * counter reset + kernels; it keeps the job pointers, which must stay valid
  * while the plan is run.  opt may be NULL.  Validation errors (any job)

@@ -83,7 +83,7 @@ class bsfp_server_stats(ctypes.Structure):
         "arena_bytes_in_use", "arena_peak_bytes", "budget_bytes", "launches")]
 
 
-BATCH_PERSISTENT, BATCH_PLAIN, BATCH_STREAMED = 0, 1, 2
+BATCH_PERSISTENT, BATCH_PLAIN, BATCH_STREAMED, BATCH_UNIFIED = 0, 1, 2, 3
 BATCH_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
 
 _lock = threading.Lock()

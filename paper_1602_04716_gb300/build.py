@@ -74,9 +74,15 @@ def _units():
     for e, m in STREAM_FORMATS:
         units.append(("stream_e%d_m%d.o" % (e, m), cu + ["-DBSFP_SE=%d" % e, "-DBSFP_SM=%d" % m,
                                                          os.path.join(CSRC, "stream_inst.cu")]))
+    for e in range(2, 9):
+        # the printed netlists of this exponent width's formats (both parts)
+        units.append(("stream_mul_e%d.o" % e, cu + ["-DBSFP_SE=%d" % e, "-DBSFP_GEN_PART=\"gen_e%d_all.cuh\"" % e,
+                                                    os.path.join(CSRC, "stream_mul_inst.cu")]))
     for opc in range(3):
         units.append(("batch_opc%d.o" % opc, cu + ["-DBSFP_BATCH_OPC=%d" % opc, os.path.join(CSRC, "batch_inst.cu")]))
-
+    for opc in range(2):
+        units.append(("ustream_opc%d.o" % opc, cu + ["-DBSFP_USTREAM_OPC=%d" % opc,
+                                                     os.path.join(CSRC, "ustream_inst.cu")]))
     for src in ("api.cu", "batch.cu", "batch_noalloc.cu", "serve.cu", "pipeline.cu", "autotune.cu", "transpose.cu", "probe.cu", "synth_gen.cu"):
         units.append((src.replace(".cu", ".o"), cu + [os.path.join(CSRC, src)]))
     return units
@@ -115,6 +121,12 @@ def generate(jobs: int | None = None) -> str:
             elif not os.path.exists(path) or os.path.getmtime(path) < newest:
                 with open(path, "w") as fh:
                     fh.write("/* no formats of this part need printed netlists */\n")
+    for e in range(2, 9):
+        # both parts of an exponent width, for the units that span every fraction width
+        path = os.path.join(GEN_DIR, "gen_e%d_all.cuh" % e)
+        if not os.path.exists(path) or os.path.getmtime(path) < newest:
+            with open(path, "w") as fh:
+                fh.write("".join('#include "%s"\n' % part_header(e, lo) for lo, _ in M_RANGES))
     todo = [t for t in todo if not os.path.exists(t[1]) or os.path.getmtime(t[1]) < newest]
     with ThreadPoolExecutor(jobs or max(1, os.cpu_count() or 1)) as ex:
         for fut in [ex.submit(_generate_one, *t) for t in todo]:

@@ -42,6 +42,11 @@ void register_int_w1(); void register_int_w17();
 /* streamed kernels, one translation unit per format (stream_inst.cu) */
 void register_stream_e4_m3(); void register_stream_e4_m4(); void register_stream_e5_m7();
 void register_stream_e5_m10(); void register_stream_e8_m7();
+/* streamed mul of the other formats of 12..24 planes, one unit per exponent
+ * width (stream_mul_inst.cu) */
+void register_stream_mul_e2(); void register_stream_mul_e3(); void register_stream_mul_e4();
+void register_stream_mul_e5(); void register_stream_mul_e6(); void register_stream_mul_e7();
+void register_stream_mul_e8();
 
 cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st);
 cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st);
@@ -61,6 +66,8 @@ static void init_tables() {
     /* after the grid-stride kernels: these extend their entries */
     register_stream_e4_m3(); register_stream_e4_m4(); register_stream_e5_m7();
     register_stream_e5_m10(); register_stream_e8_m7();
+    register_stream_mul_e2(); register_stream_mul_e3(); register_stream_mul_e4(); register_stream_mul_e5();
+    register_stream_mul_e6(); register_stream_mul_e7(); register_stream_mul_e8();
 }
 
 /* The streamed kernel is taken only when every SM gets at least this many
@@ -286,7 +293,7 @@ static bsfp_status prepare_binop_impl(const bsfp_format& f, int op, const uint32
 }
 
 static void pick_shape(const Shape& sh, const BinopEntry* e, int64_t S, int* wpt, int* bps) {
-    *wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
+    *wpt = (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : (e->preferred ? e->preferred : e->default_wpt);
     *bps = sh.bps;
     if (*wpt == VARIANT_STREAMED) {
         const int64_t tiles = (S + e->stream_tw - 1) / e->stream_tw;
@@ -619,7 +626,7 @@ int32_t bsfp_variant(bsfp_format f, int32_t op) {
     const BinopEntry* e = entry_for(f, opc);
     if (!e) return 0;
     const Shape sh = load_shape(f, opc);
-    return (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : e->default_wpt;
+    return (sh.wpt && (e->wpt_mask & (unsigned)sh.wpt)) ? sh.wpt : (e->preferred ? e->preferred : e->default_wpt);
 }
 
 bsfp_status bsfp_set_variant(bsfp_format f, int32_t op, int32_t wpt, int32_t blocks_per_sm) {

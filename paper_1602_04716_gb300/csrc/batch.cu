@@ -13,6 +13,7 @@
 #include "bsfp.h"
 #include "internal.h"
 #include "stream.cuh"
+#include "ustream.cuh"
 
 namespace bsfp {
 
@@ -30,6 +31,13 @@ batch_launch_fn batch_launcher(int opc, int wpt) {
         case OPC_FMA2: return batch_launcher_opc2(wpt);
     }
     return nullptr;
+}
+
+UStreamEntry ustream_entry_opc0();
+UStreamEntry ustream_entry_opc1();
+
+UStreamEntry ustream_entry(int opc) {
+    return opc == OPC_ADDSUB ? ustream_entry_opc0() : (opc == OPC_MUL ? ustream_entry_opc1() : UStreamEntry());
 }
 
 const void* batch_kernel_ptr(int opc, int wpt) {
@@ -80,7 +88,8 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     bsfp_batch_options o = {BSFP_BATCH_PERSISTENT, 2, 0};
     if (opt) o = *opt;
     if (o.wpt == 0) o.wpt = 2;
-    if ((o.mode != BSFP_BATCH_PERSISTENT && o.mode != BSFP_BATCH_PLAIN && o.mode != BSFP_BATCH_STREAMED) ||
+    if ((o.mode != BSFP_BATCH_PERSISTENT && o.mode != BSFP_BATCH_PLAIN && o.mode != BSFP_BATCH_STREAMED &&
+         o.mode != BSFP_BATCH_UNIFIED) ||
         (o.wpt != 1 && o.wpt != 2) || o.blocks_per_sm < 0 || o.blocks_per_sm > 64)
         return BSFP_ERR_SIZE;
 
@@ -99,13 +108,21 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         std::vector<int32_t> tmap;
     };
     std::vector<SGroup> sgroups;
+    const bool unified = o.mode == BSFP_BATCH_UNIFIED;
+    const bool streamed = o.mode == BSFP_BATCH_STREAMED || unified;
+    constexpr int UGROUP = OPC_COUNT + 1;   /* group[i] = UGROUP + op class: a unified kernel */
     for (int32_t i = 0; i < njobs; ++i) {
         const bsfp_job& j = jobs[i];
         PreparedOp& po = prep[(size_t)i];
         const bsfp_status st = prepare_binop(j.f, j.op, j.a, j.b, j.c, j.out, j.n, &po);
         if (st != BSFP_OK) return st;
         if (po.skip) continue;
-        if (o.mode == BSFP_BATCH_STREAMED && (po.opc == OPC_ADDSUB || po.opc == OPC_MUL) &&
+        if (unified && (po.opc == OPC_ADDSUB || po.opc == OPC_MUL) &&
+            batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd) >= 0) {
+            group[(size_t)i] = UGROUP + po.opc;
+            continue;
+        }
+        if (streamed && (po.opc == OPC_ADDSUB || po.opc == OPC_MUL) &&
             (po.entry->wpt_mask & (unsigned)VARIANT_STREAMED) && po.entry->stream_batch_launch) {
             size_t gi = 0;
             while (gi < sgroups.size() && sgroups[gi].e != po.entry) ++gi;
@@ -165,6 +182,40 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         if (e != cudaSuccess) return set_cuda_error(e);
     }
 
+    /* unified kernels: per op class, the jobs' descriptors and tile map (tile
+     * widths per kind from the kernel's shape) */
+    UStreamEntry uent[2];
+    std::vector<JobDesc> udesc[2];
+    std::vector<int32_t> umap[2];
+    for (int32_t i = 0; i < njobs && unified; ++i) {
+        const int g = group[(size_t)i] - UGROUP;
+        if (g < 0 || g > 1) continue;
+        if (!uent[g].launch) {
+            uent[g] = ustream_entry(g);
+            if (!uent[g].launch) return BSFP_ERR_UNSUPPORTED;
+            const cudaError_t e = uent[g].prepare();
+            if (e != cudaSuccess) return set_cuda_error(e);
+        }
+        const bsfp_job& j = jobs[i];
+        const BinopArgs& a = prep[(size_t)i].args;
+        JobDesc d;
+        memset(&d, 0, sizeof d);
+        d.a = a.a;
+        d.b = a.b;
+        d.out = a.out;
+        d.S = a.S;
+        d.nwords = a.nwords;
+        d.tile0 = (int64_t)umap[g].size();
+        d.tailmask = a.tailmask;
+        d.negb = a.negb;
+        d.kind = batch_kind(j.f.exp_bits, j.f.man_bits, j.f.rnd);
+        const int64_t tw = uent[g].tw[d.kind];
+        const int64_t nt = (a.S + tw - 1) / tw;
+        const int32_t idx = (int32_t)udesc[g].size();
+        udesc[g].push_back(d);
+        for (int64_t t = 0; t < nt; ++t) umap[g].push_back(idx);
+    }
+
     /* tiles per group */
     const int64_t TILE = 128LL * o.wpt * BATCH_ROUNDS;
     std::vector<JobDesc> desc[OPC_COUNT];
@@ -210,6 +261,15 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         off_smap[g] = total;
         total = align_up(total + sgroups[g].tmap.size() * sizeof(int32_t), 256);
     }
+    size_t off_udesc[2], off_umap[2], off_ucnt[2];
+    for (int g = 0; g < 2; ++g) {
+        off_udesc[g] = total;
+        total = align_up(total + udesc[g].size() * sizeof(JobDesc), 256);
+        off_umap[g] = total;
+        total = align_up(total + umap[g].size() * sizeof(int32_t), 256);
+        off_ucnt[g] = total;
+        total = align_up(total + sizeof(unsigned long long), 256);
+    }
 
     bsfp_batch_plan p = new bsfp_batch_plan_st();
     cudaError_t err = cudaMalloc(&p->dev, total);
@@ -230,6 +290,14 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
                          cudaMemcpyHostToDevice);
         if (err == cudaSuccess)
             err = cudaMemcpy(base + off_smap[g], sgroups[g].tmap.data(), sgroups[g].tmap.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice);
+    }
+    for (int g = 0; g < 2 && err == cudaSuccess; ++g) {
+        if (udesc[g].empty()) continue;
+        err = cudaMemcpy(base + off_udesc[g], udesc[g].data(), udesc[g].size() * sizeof(JobDesc),
+                         cudaMemcpyHostToDevice);
+        if (err == cudaSuccess)
+            err = cudaMemcpy(base + off_umap[g], umap[g].data(), umap[g].size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice);
     }
     if (err != cudaSuccess) {
@@ -265,7 +333,8 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     bsfp_status st = BSFP_OK;
     /* side streams and events for the streamed groups' parallel branches */
     constexpr int NBRANCH = 8;
-    const int nside = (int)(sgroups.size() < (size_t)NBRANCH ? sgroups.size() : (size_t)NBRANCH);
+    const size_t nbranches = sgroups.size() + (udesc[0].empty() ? 0 : 1) + (udesc[1].empty() ? 0 : 1);
+    const int nside = (int)(nbranches < (size_t)NBRANCH ? nbranches : (size_t)NBRANCH);
     cudaStream_t side[NBRANCH] = {};
     cudaEvent_t fork = nullptr, join[NBRANCH] = {};
     for (int i = 0; i < nside && err == cudaSuccess; ++i) {
@@ -285,13 +354,29 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
             for (int i = 0; i < nside && e2 == cudaSuccess; ++i) e2 = cudaStreamWaitEvent(side[i], fork, 0);
             if (e2 != cudaSuccess) st = set_cuda_error(e2);
         }
+        size_t branch = 0;
+        /* the unified kernels first: the longest branches */
+        for (int g = 0; g < 2 && st == BSFP_OK; ++g) {
+            if (udesc[g].empty()) continue;
+            const int64_t ntiles = (int64_t)umap[g].size();
+            const int64_t sms = device_num_sms();
+            cudaStream_t bs = side[branch++ % NBRANCH];
+            unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + off_ucnt[g]);
+            cudaError_t e2 = cudaMemsetAsync(cnt, 0, sizeof *cnt, bs);
+            if (e2 == cudaSuccess)
+                e2 = uent[g].launch(reinterpret_cast<const JobDesc*>(base + off_udesc[g]),
+                                    reinterpret_cast<const int32_t*>(base + off_umap[g]), ntiles, cnt,
+                                    current_fault_word(), (int)(ntiles < sms ? ntiles : sms), bs);
+            if (e2 != cudaSuccess) st = set_cuda_error(e2);
+            else p->launches += 1;
+        }
         for (size_t g = 0; g < sgroups.size() && st == BSFP_OK; ++g) {
             const int64_t ntiles = (int64_t)sgroups[g].tmap.size();
             const int64_t sms = device_num_sms();
             const cudaError_t e2 = sgroups[g].e->stream_batch_launch(
                 reinterpret_cast<const StreamJob*>(base + off_sjobs[g]),
                 reinterpret_cast<const int32_t*>(base + off_smap[g]), ntiles, sgroups[g].fault,
-                (int)(ntiles < sms ? ntiles : sms), side[g % NBRANCH]);
+                (int)(ntiles < sms ? ntiles : sms), side[branch++ % NBRANCH]);
             if (e2 != cudaSuccess) st = set_cuda_error(e2);
             else p->launches += 1;
         }

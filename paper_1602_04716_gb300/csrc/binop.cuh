@@ -204,7 +204,8 @@ struct BinopEntry {
     binop_kernel_fn kernel;   /* the __global__ function, for occupancy queries */
     unsigned wpt_mask;        /* compiled variants: bit 0 = 1, bit 1 = 2, bit 2 = 4,
                                  bit 3 = the streamed kernel */
-    int default_wpt;
+    int default_wpt;          /* the grid-stride default (and the streamed variant's fallback) */
+    int preferred = 0;        /* the variant a call takes when no shape is set (0 = default_wpt) */
     /* the streamed kernel, where compiled (filled by stream_inst.cu) */
     stream_launch_fn stream_launch = nullptr;
     stream_prepare_fn stream_prepare = nullptr;   /* opts in to its shared memory */

@@ -42,8 +42,16 @@
 
 namespace bsfp {
 
-/* Formats and op classes compiled with a streamed kernel. */
+/* Formats and op classes compiled with a streamed kernel: the tuned formats
+ * of at most 16 planes (add/sub and mul, every mode, and their job-list
+ * form), and mul under RN and RZ of every other format of 12 to 24 planes
+ * (stream_mul_inst.cu) -- the band where the multiplier sits near the
+ * crossover of logic and HBM bounds and the grid-stride kernel, with few
+ * warps resident, leaves both pipes idle part of the time. */
 constexpr bool stream_format(int E, int M) { return tuned_format(E, M) && 1 + E + M <= 16; }
+constexpr bool stream_mul_format(int E, int M) {
+    return !tuned_format(E, M) && 1 + E + M >= 12 && 1 + E + M <= 24;
+}
 constexpr bool stream_opc(int opc) { return opc == OPC_ADDSUB || opc == OPC_MUL; }
 
 template <int E, int M, int OPC>
@@ -55,9 +63,13 @@ struct StreamShape {
      * adder (deeper ring, and its light circuit needs fewer warps) and 15 x 2
      * for mul (more warps feed its logic pipe); 12 x 2 for B = 16, except
      * mul 1/8/7 at 14 x 2 (1/5/10 mul gained nothing and its job-list form
-     * spills there, and the adders stream at the copy bandwidth with 12) */
+     * spills there, and the adders stream at the copy bandwidth with 12).
+     * Wider formats: 8 x 2 up to 24 planes, 6 x 2 beyond, so that the ring
+     * of 2B planes fits and each thread may hold the wide multipliers'
+     * registers. */
     static constexpr int NC = B <= 9 ? 11
-                            : (B <= 13 ? (OPC == OPC_ADDSUB ? 11 : 15) : ((OPC == OPC_MUL && E == 8) ? 14 : 12));
+                            : (B <= 13 ? (OPC == OPC_ADDSUB ? 11 : 15)
+                                       : (B <= 16 ? ((OPC == OPC_MUL && E == 8) ? 14 : 12) : (B <= 24 ? 8 : 6)));
     static constexpr int NST = B <= 9 ? 4 : ((B <= 13 && OPC == OPC_ADDSUB) ? 3 : 2);   /* ring stages */
     static constexpr int NIN = 2 * B;                               /* input planes per tile */
     static constexpr int TW = 32 * NC * WPT;                        /* words per plane per tile */

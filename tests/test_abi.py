@@ -120,7 +120,12 @@ def test_variants_and_overrides():
     assert bs.bsfp_variants_compiled(bs.Format(8, 23), "mul") == [1, 2]
     assert bs.bsfp_variant(f, "add") in (1, 2, 4, bs.VARIANT_STREAMED)
     g = bs.Format(6, 9)
-    assert len(bs.bsfp_variants_compiled(g, "mul")) == 1
+    # a format outside the tuned set: its default words per thread, and (16 planes) the streamed mul,
+    # which its mul calls take by default
+    assert bs.bsfp_variants_compiled(g, "mul") == [2, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variant(g, "mul") == bs.VARIANT_STREAMED
+    assert len(bs.bsfp_variants_compiled(g, "add")) == 1
+    assert bs.bsfp_variants_compiled(bs.Format(3, 5), "mul") == [2]   # 9 planes: below the streamed band
     with pytest.raises(bs.BsfpError):
         bs.bsfp_set_variant(g, "mul", 4)
     bs.bsfp_set_variant(f, "mul", 1, 3)
@@ -255,11 +260,12 @@ def test_autotune_arguments_and_cache_loading(tmp_path):
 
 
 def test_batch_plan_options_validated_before_any_cuda_call():
-    """Plan modes are PERSISTENT (0), PLAIN (1) and STREAMED (2); anything
-    else, or a bad shape, is refused before a job is looked at."""
+    """Plan modes are PERSISTENT (0), PLAIN (1), STREAMED (2) and UNIFIED (3);
+    anything else, or a bad shape, is refused before a job is looked at."""
     L = _binding._lib()
     h = ctypes.c_void_p()
-    for mode, wpt, bps in ((3, 0, 0), (-1, 0, 0), (bs.BATCH_STREAMED, 3, 0), (bs.BATCH_STREAMED, 0, 65)):
+    for mode, wpt, bps in ((4, 0, 0), (-1, 0, 0), (bs.BATCH_STREAMED, 3, 0), (bs.BATCH_STREAMED, 0, 65),
+                           (bs.BATCH_UNIFIED, 3, 0)):
         opt = bs.bsfp_batch_options(mode, wpt, bps)
         assert L.bsfp_batch_plan_create(None, 0, ctypes.byref(opt), ctypes.byref(h)) == bs.ERR_SIZE
     assert L.bsfp_batch_plan_create(None, -1, None, ctypes.byref(h)) == bs.ERR_SIZE

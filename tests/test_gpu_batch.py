@@ -161,6 +161,54 @@ def test_streamed_plan_sends_small_groups_to_the_persistent_kernels():
     plan.free()
 
 
+def test_unified_plan_matches_oracle_and_replays():
+    """BSFP_BATCH_UNIFIED: the RN/RZ add/sub jobs of the five batched formats
+    in one streamed launch and their mul jobs in another, whatever the
+    format; tiles (of a width per format) from an atomic counter.  The other
+    jobs go as in the streamed plan.  Every job exact, and again on a replay
+    (the counters are cleared by the graph)."""
+    jobs = _make_batch(220, 5300)
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_UNIFIED)
+    live = [j for j in jobs if j["n"] > 0]
+    batch = [j for j in live if (j["E"], j["M"]) in bs.BATCH_FORMATS]
+    unified = {j["op"] == "mul" for j in batch if j["op"] in ("add", "sub", "mul") and j["rnd"] < 2}
+    ftz_groups = {(j["E"], j["M"], j["rnd"], j["op"] == "mul") for j in batch
+                  if j["op"] in ("add", "sub", "mul") and j["rnd"] > 1}
+    persistent = 1 if any(j["op"] == "fma2" and j["rnd"] < 2 for j in batch) else 0
+    plain = [j for j in live if (j["E"], j["M"]) not in bs.BATCH_FORMATS or j["op"] == "div" or
+             (j["op"] == "fma2" and j["rnd"] > 1)]
+    assert plan.launches == len(unified) + len(ftz_groups) + persistent + len(plain)
+    for _ in range(2):
+        _clear(jobs)
+        plan.run()
+        torch.cuda.synchronize()
+        _check_all(jobs)
+    assert bs.bsfp_fault_status() == 0
+    plan.free()
+
+
+def test_unified_plan_many_tiles_per_block():
+    """Jobs up to 2^20 elements of the batched formats, RN/RZ add, sub and
+    mul only: many more tiles than SMs, of every kind interleaved, so every
+    block goes round its ring many times and the last tile of many jobs is
+    ragged."""
+    jobs = _make_batch(64, 7400, max_len=1 << 20, extra_formats=())
+    for i, j in enumerate(jobs):
+        j["rnd"] = j["rnd"] & 1
+        if j["op"] in ("fma2", "div"):
+            j["op"] = ("add", "sub", "mul")[i % 3]
+    arr, nj = _ctypes_jobs(jobs)
+    plan = bs.BatchPlan(arr, nj, bs.BATCH_UNIFIED)
+    assert plan.launches == len({j["op"] == "mul" for j in jobs if j["n"] > 0})
+    _clear(jobs)
+    plan.run()
+    torch.cuda.synchronize()
+    _check_all(jobs)
+    assert bs.bsfp_fault_status() == 0
+    plan.free()
+
+
 def test_plain_graph_and_plain_launches_match():
     jobs = _make_batch(120, 8000)
     arr, nj = _ctypes_jobs(jobs)

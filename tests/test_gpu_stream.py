@@ -62,10 +62,15 @@ def test_streamed_variant_is_compiled_where_documented():
                 assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(f, op), (E, M, rnd, op)
             for op in ("fma2", "div"):
                 assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(f, op)
-    for E, M in [(8, 23), (6, 9), (3, 2)]:
+    for E, M in [(8, 23), (3, 2)]:
         assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(bs.Format(E, M), "mul")
+    # outside the tuned set: the streamed mul (RN, RZ) for 12..24 planes, no streamed add
+    assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(6, 9, 1), "mul")
+    assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(bs.Format(6, 9), "add")
     with pytest.raises(bs.BsfpError):
-        bs.bsfp_set_variant(bs.Format(6, 9), "mul", bs.VARIANT_STREAMED)
+        bs.bsfp_set_variant(bs.Format(6, 9), "add", bs.VARIANT_STREAMED)
+    with pytest.raises(bs.BsfpError):
+        bs.bsfp_set_variant(bs.Format(3, 2), "mul", bs.VARIANT_STREAMED)
 
 
 @pytest.mark.parametrize("E,M", STREAM_FORMATS)
@@ -244,3 +249,48 @@ def test_in_place_output(op):
     got = oracle.unpack(B, pa.cpu().numpy().view(np.uint32), n)[idx]
     assert (got == oracle.binop(op, E, M, 0, a[idx], b[idx])).all()
     bs.bsfp_set_variant(f, op, 0, 0)
+
+
+def _streamed_mul_formats():
+    fm = []
+    for E in range(2, 9):
+        for M in range(1, 24):
+            if 1 + E + M <= 32 and (E, M) not in STREAM_FORMATS and \
+                    bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(E, M), "mul"):
+                fm.append((E, M))
+    return fm
+
+
+def test_streamed_mul_covers_the_band_of_12_to_24_planes():
+    fm = _streamed_mul_formats()
+    assert fm and all(12 <= 1 + E + M <= 24 for E, M in fm)
+    assert len(fm) == sum(1 for E in range(2, 9) for M in range(1, 24)
+                          if 12 <= 1 + E + M <= 24 and (E, M) not in STREAM_FORMATS + [(8, 23)])
+
+
+@pytest.mark.parametrize("E", range(2, 9))
+def test_streamed_mul_of_every_format_in_the_band_vs_oracle(E):
+    """Formats of 12..24 planes outside the tuned set have a streamed mul (the
+    default up to 16 planes, the autotuner's choice beyond).  For each of
+    them, RN and RZ, forced streamed at every size: inside one tile, and three
+    tiles plus a ragged tail, every word of the output planes (padding
+    included) against the oracle."""
+    for (e, M) in _streamed_mul_formats():
+        if e != E:
+            continue
+        B = 1 + E + M
+        TW, _ = shape(E, M, "mul")
+        for n in (77, 3 * 32 * TW + 77):
+            a = synth.fp_values(E, M, n, 900 + M).astype(np.uint32)
+            b = synth.fp_values(E, M, n, 950 + M).astype(np.uint32)
+            pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+            for rnd in (0, 1):
+                f = bs.Format(E, M, rnd)
+                bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED)
+                out = torch.full_like(pa, -1)
+                bs.bsfp_mul(f, pa, pb, out, n)
+                bs.bsfp_set_variant(f, "mul", 0, 0)
+                got = out.cpu().numpy().view(np.uint32).reshape(B, -1)
+                want = oracle.pack(B, oracle.binop("mul", E, M, rnd, a, b))
+                assert (got == want).all(), "mul 1/%d/%d rnd=%d n=%d" % (E, M, rnd, n)
+    assert bs.bsfp_fault_status() == 0
