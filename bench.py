@@ -50,9 +50,11 @@ WORKLOAD = ("plain single-format at scale: bs_add + bs_mul (RN) on 1/4/4 and 1/5
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from ncu captures at 2^26 elements
 # scaled x4 to the 2^28-element launch, keyed by (E, M, op, kernel variant): a figure stands only
 # for the kernel it was taken on, as it now stands (profiles/traffic_bench_kernels_2p26.md: medians of
-# five launches each); a kernel not listed reports null.
-NCU_TRAFFIC = {(5, 7, "add", 2): (218.124544e6 + 69.806080e6) * 4,
-               (5, 7, "mul", 8): (218.133504e6 + 63.068928e6) * 4}
+# six launches each); a kernel not listed reports null.
+NCU_TRAFFIC = {(4, 4, "add", 8): (151.015168e6 + 35.996672e6) * 4,
+               (4, 4, "mul", 8): (151.014912e6 + 36.211712e6) * 4,
+               (5, 7, "add", 8): (218.130432e6 + 66.021376e6) * 4,
+               (5, 7, "mul", 8): (218.155776e6 + 62.862592e6) * 4}
 
 
 class DeviceTimer:
@@ -460,6 +462,8 @@ def run_section(bs, torch, args, rank):
         res = run_sweep(bs, torch, args, rank, hbm, lop3_rate(bs, torch))
     elif args.section == "batched":
         res = run_batched(bs, torch, args, rank, hbm)
+    elif args.section == "e2e":
+        res = run_e2e(bs, torch, n, rank, args)
     else:
         res = run_serving(bs, torch, args, rank)
     if rank == 0:
@@ -815,8 +819,29 @@ def host_link_rates(torch, pinned, reps=3):
             t1.record()
             t1.synchronize()
             best[kind] = min(best[kind], t0.elapsed_time(t1))
-    del dev
-    return {"bytes": nbytes, "h2d_gbs": nbytes / best["h2d"] / 1e6, "d2h_gbs": nbytes / best["d2h"] / 1e6}
+    # both directions at once, on two streams (the pipeline overlaps them)
+    dev2 = torch.empty_like(pinned, device="cuda")
+    back = torch.empty_like(pinned).pin_memory()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    both = float("inf")
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        s1.wait_event(t0)
+        s2.wait_event(t0)
+        with torch.cuda.stream(s1):
+            dev.copy_(pinned, non_blocking=True)
+        with torch.cuda.stream(s2):
+            back.copy_(dev2, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(s1)
+        torch.cuda.current_stream().wait_stream(s2)
+        t1.record()
+        t1.synchronize()
+        both = min(both, t0.elapsed_time(t1))
+    del dev, dev2, back
+    return {"bytes": nbytes, "h2d_gbs": nbytes / best["h2d"] / 1e6, "d2h_gbs": nbytes / best["d2h"] / 1e6,
+            "both_directions_gbs": 2 * nbytes / both / 1e6}
 
 
 def run_e2e(bs, torch, n, rank, args):
@@ -855,17 +880,22 @@ def run_e2e(bs, torch, n, rank, args):
         step()
     torch.cuda.synchronize()
     k = max(1, args.e2e_steps)
+    per_step = []
     t = time.perf_counter()
     for _ in range(k):
+        t1 = time.perf_counter()
         step()
+        per_step.append((time.perf_counter() - t1) * 1e3)
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t) / k
     pipe.close()
     link = host_link_rates(torch, host_in[FORMATS[-1]][0])
     link_ms = 1e3 * (h2d / (link["h2d_gbs"] * 1e9) + d2h / (link["d2h_gbs"] * 1e9))
     link["serial_copy_ms_per_step"] = link_ms
+    link["overlapped_copy_ms_per_step"] = 1e3 * (h2d + d2h) / (link["both_directions_gbs"] * 1e9)
     return {"value": len(FORMATS) * len(OPS) * n / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k, "host_link": link,
+            "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k, "step_ms": per_step,
+            "host_link": link,
             "path": "pinned host -> bsfp_pipeline_run (chunks of %d over %d streams: H2D, bsfp_pack, "
                     "bsfp_add + bsfp_mul, bsfp_unpack, D2H) -> pinned host, per format"
                     % (args.e2e_chunk or (1 << 23), args.e2e_depth or 4)}
@@ -901,7 +931,7 @@ def main(argv=None):
                     help="elements per vector in the format sweep (0 skips it)")
     ap.add_argument("--sweep-out", default=None, help="write the full sweep table (JSON) here")
     ap.add_argument("--section", default=None,
-                    choices=["conversions", "small", "integers", "sweep", "batched", "serving"],
+                    choices=["conversions", "small", "integers", "sweep", "batched", "serving", "e2e"],
                     help="run only this section of the bench and print it (no main timed loop)")
     ap.add_argument("--section-reps", type=int, default=5, help="timed launches per kernel in --section conversions")
     args = ap.parse_args(argv)
