@@ -244,7 +244,7 @@ void bsfp_batch_free(bsfp_batch_plan plan);
 bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t s);
 
 /* Limits of bsfp_batch_run_noalloc: jobs per call, and tiles per call (one
- * tile = 32,768 elements of one job, rounded up per job, counting only jobs in
+ * tile = 8,192 elements of one job, rounded up per job, counting only jobs in
  * the persistent formats).  Its fixed scratch is sized from these: about
  * 1.5 MB of device memory per GPU that loads the library. */
 #define BSFP_NOALLOC_MAX_JOBS 4096
@@ -338,7 +338,8 @@ typedef struct {
     int64_t budget_bytes;    /* result arena, bytes (> 0) */
     int32_t slots;           /* micro-batches in flight at once, 1..16 (0 = 4) */
     int32_t max_batch_jobs;  /* requests per micro-batch, 1..4096 (0 = 1024) */
-    int32_t max_batch_tiles; /* 32,768-element tiles per micro-batch, 128..2^20 (0 = 2^16) */
+    int32_t max_batch_tiles; /* tiles of 8,192 elements (4,096 with wpt 1) per micro-batch, 128..2^20
+                                (0 = 2^18) */
     int32_t wpt;             /* words per thread of the persistent kernels, 1 or 2 (0 = 2) */
     /* Admission.  While fewer than eager_slots micro-batches are in flight a
      * free slot takes the pending requests at once (latency first).  With

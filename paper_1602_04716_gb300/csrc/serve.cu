@@ -396,7 +396,7 @@ bsfp_status bsfp_server_create(const bsfp_server_options* opt, bsfp_server* out)
     if (opt) o = *opt;
     if (o.slots == 0) o.slots = 4;
     if (o.max_batch_jobs == 0) o.max_batch_jobs = 1024;
-    if (o.max_batch_tiles == 0) o.max_batch_tiles = 1 << 16;
+    if (o.max_batch_tiles == 0) o.max_batch_tiles = 1 << 18;
     if (o.wpt == 0) o.wpt = 2;
     if (o.eager_slots == 0) o.eager_slots = o.slots;
     if (o.batch_wait_us == 0) o.batch_wait_us = 20;

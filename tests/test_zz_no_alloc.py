@@ -92,7 +92,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch_before_launching():
     assert L.bsfp_batch_run_noalloc(jobs, bs.NOALLOC_MAX_JOBS + 1, None) == bs.ERR_SIZE
     assert L.bsfp_batch_run_noalloc(jobs, -1, None) == bs.ERR_SIZE
     assert L.bsfp_batch_run_noalloc(ctypes.cast(None, ctypes.POINTER(bs.bsfp_job)), 3, None) == bs.ERR_NULL
-    # one job of 2^40 elements needs 2^25 tiles: refused by the host-side
+    # one job of 2^40 elements needs 2^27 tiles: refused by the host-side
     # check, so the (aligned, never dereferenced) addresses are not touched
     big, nj = bs.make_jobs([(bs.Format(4, 3), "add", 256, 512, None, 768, 1 << 40)])
     before = bs.bsfp_launch_count()
