@@ -45,6 +45,11 @@ def part_header(e, lo):
     return "gen_e%d_m%d.cuh" % (e, lo)
 
 
+def div_header(e, lo):
+    """div (RN, RZ) of the part's other formats, printed for its division unit"""
+    return "gen_div_e%d_m%d.cuh" % (e, lo)
+
+
 def nvcc() -> str:
     for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
         if c and os.path.exists(c):
@@ -61,8 +66,12 @@ def _units():
     for e in range(2, 9):
         for lo, hi in M_RANGES:
             units.append(("binop_e%d_m%d.o" % (e, lo),
-                          cu + ["-DBSFP_E=%d" % e, "-DBSFP_M_LO=%d" % lo, "-DBSFP_M_HI=%d" % hi,
+                          cu + ["-DBSFP_E=%d" % e, "-DBSFP_M_LO=%d" % lo, "-DBSFP_M_HI=%d" % hi, "-DBSFP_NO_DIV",
                                 '-DBSFP_GEN_PART="%s"' % part_header(e, lo),
+                                os.path.join(CSRC, "binop_inst.cu")]))
+            units.append(("binop_div_e%d_m%d.o" % (e, lo),
+                          cu + ["-DBSFP_E=%d" % e, "-DBSFP_M_LO=%d" % lo, "-DBSFP_M_HI=%d" % hi, "-DBSFP_DIV_UNIT",
+                                '-DBSFP_GEN_PART="%s"' % div_header(e, lo),
                                 os.path.join(CSRC, "binop_inst.cu")]))
         units.append(("gatecount_e%d.o" % e,
                       ["g++", "-std=c++17", "-O1", "-fPIC", "-I", CSRC, "-DBSFP_E=%d" % e, "-c",
@@ -95,7 +104,7 @@ def _deps():
 def _generate_one(defines, out_path, tag):
     """Compile circuitgen with the given format lists and print one header."""
     tool = os.path.join(BUILD, "circuitgen_" + tag)
-    subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", CSRC, *defines, os.path.join(CSRC, "circuitgen.cpp"),
+    subprocess.check_call(["g++", "-std=c++17", "-O0", "-w", "-I", CSRC, *defines, os.path.join(CSRC, "circuitgen.cpp"),
                            "-o", tool])
     tmp = out_path + ".tmp"
     subprocess.check_call([tool, tmp])
@@ -115,12 +124,15 @@ def generate(jobs: int | None = None) -> str:
     for e in range(2, 9):
         for lo, hi in M_RANGES:
             ys = " ".join("Y(%d, %d)" % fm for fm in part_formats(e, lo, hi))
-            path = os.path.join(GEN_DIR, part_header(e, lo))
-            if ys:
-                todo.append((["-DBSFP_GEN_ADDMUL=" + ys], path, "e%d_m%d" % (e, lo)))
-            elif not os.path.exists(path) or os.path.getmtime(path) < newest:
-                with open(path, "w") as fh:
-                    fh.write("/* no formats of this part need printed netlists */\n")
+            zs = ys.replace("Y(", "Z(")
+            for lst, macro, name, tag in ((ys, "-DBSFP_GEN_ADDMUL=", part_header(e, lo), "e%d_m%d" % (e, lo)),
+                                          (zs, "-DBSFP_GEN_DIV=", div_header(e, lo), "div_e%d_m%d" % (e, lo))):
+                path = os.path.join(GEN_DIR, name)
+                if lst:
+                    todo.append(([macro + lst], path, tag))
+                elif not os.path.exists(path) or os.path.getmtime(path) < newest:
+                    with open(path, "w") as fh:
+                        fh.write("/* no formats of this part need printed netlists */\n")
     for e in range(2, 9):
         # both parts of an exponent width, for the units that span every fraction width
         path = os.path.join(GEN_DIR, "gen_e%d_all.cuh" % e)

@@ -31,8 +31,10 @@ typedef cudaError_t (*int_launch_fn)(const uint32_t* a, const uint32_t* b, uint3
 int_launch_fn g_int_table[33][3];
 
 /* Each exponent width is compiled as two translation units, M in [1, 11]
- * and [12, 23]; each fills its part of the table. */
-#define BSFP_DECL_REG(E) void register_e##E##_m1(); void register_e##E##_m12();
+ * and [12, 23], and its division as two more; each fills its part of the
+ * table. */
+#define BSFP_DECL_REG(E) void register_e##E##_m1(); void register_e##E##_m12(); \
+    void register_div_e##E##_m1(); void register_div_e##E##_m12();
 BSFP_DECL_REG(2) BSFP_DECL_REG(3) BSFP_DECL_REG(4) BSFP_DECL_REG(5) BSFP_DECL_REG(6) BSFP_DECL_REG(7)
 BSFP_DECL_REG(8)
 #undef BSFP_DECL_REG
@@ -60,6 +62,13 @@ static void init_tables() {
     register_e6_m1(); register_e6_m12();
     register_e7_m1(); register_e7_m12();
     register_e8_m1(); register_e8_m12();
+    register_div_e2_m1(); register_div_e2_m12();
+    register_div_e3_m1(); register_div_e3_m12();
+    register_div_e4_m1(); register_div_e4_m12();
+    register_div_e5_m1(); register_div_e5_m12();
+    register_div_e6_m1(); register_div_e6_m12();
+    register_div_e7_m1(); register_div_e7_m12();
+    register_div_e8_m1(); register_div_e8_m12();
     register_conv_e2(); register_conv_e3(); register_conv_e4(); register_conv_e5();
     register_conv_e6(); register_conv_e7(); register_conv_e8();
     register_int_w1(); register_int_w17();

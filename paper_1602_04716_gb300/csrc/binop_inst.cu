@@ -21,12 +21,24 @@
 
 namespace bsfp {
 
+/* Op classes this unit instantiates: all four, or only division
+ * (-DBSFP_DIV_UNIT, a unit of its own so that the printed division circuits
+ * compile in parallel with the others), or all but division
+ * (-DBSFP_NO_DIV, the units that a division unit pairs with). */
+#if defined(BSFP_DIV_UNIT)
+constexpr bool unit_has(int opc) { return opc == OPC_DIV; }
+#elif defined(BSFP_NO_DIV)
+constexpr bool unit_has(int opc) { return opc != OPC_DIV; }
+#else
+constexpr bool unit_has(int) { return true; }
+#endif
+
 template <int E, int M, int R>
 static void fill_mode() {
-    g_binop_table[E][M][R][OPC_ADDSUB] = make_entry<E, M, R, OPC_ADDSUB>();
-    g_binop_table[E][M][R][OPC_MUL] = make_entry<E, M, R, OPC_MUL>();
-    g_binop_table[E][M][R][OPC_FMA2] = make_entry<E, M, R, OPC_FMA2>();
-    g_binop_table[E][M][R][OPC_DIV] = make_entry<E, M, R, OPC_DIV>();
+    if constexpr (unit_has(OPC_ADDSUB)) g_binop_table[E][M][R][OPC_ADDSUB] = make_entry<E, M, R, OPC_ADDSUB>();
+    if constexpr (unit_has(OPC_MUL)) g_binop_table[E][M][R][OPC_MUL] = make_entry<E, M, R, OPC_MUL>();
+    if constexpr (unit_has(OPC_FMA2)) g_binop_table[E][M][R][OPC_FMA2] = make_entry<E, M, R, OPC_FMA2>();
+    if constexpr (unit_has(OPC_DIV)) g_binop_table[E][M][R][OPC_DIV] = make_entry<E, M, R, OPC_DIV>();
 }
 
 template <int E, int M>
@@ -47,7 +59,12 @@ static void fill_format() {
 #define BSFP_CAT(a, b) BSFP_CAT2(a, b)
 #define BSFP_CAT3(a, b, c) BSFP_CAT(BSFP_CAT(a, b), c)
 
-/* register_e<E>_m<LO>: called once by the dispatcher */
+/* register_e<E>_m<LO> (register_div_e<E>_m<LO> for a division unit):
+ * called once by the dispatcher */
+#if defined(BSFP_DIV_UNIT)
+void BSFP_CAT3(BSFP_CAT(register_div_e, BSFP_E), _m, BSFP_M_LO)() { fill_format<BSFP_E, BSFP_M_LO>(); }
+#else
 void BSFP_CAT3(BSFP_CAT(register_e, BSFP_E), _m, BSFP_M_LO)() { fill_format<BSFP_E, BSFP_M_LO>(); }
+#endif
 
 }  // namespace bsfp

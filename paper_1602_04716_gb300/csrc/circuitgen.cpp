@@ -16,15 +16,17 @@
  * at G.  This plays the part of the paper's generator (Sec. 5.1: a
  * configuration of formats in, generated code for them out).
  *
- * Usage: circuitgen OUT.cuh    (formats from -DBSFP_GEN_FORMATS="X(E, M) ..."
- *                               and/or -DBSFP_GEN_ADDMUL="Y(E, M) ...")
+ * Usage: circuitgen OUT.cuh    (formats from -DBSFP_GEN_FORMATS="X(E, M) ...",
+ *                               -DBSFP_GEN_ADDMUL="Y(E, M) ..." and/or
+ *                               -DBSFP_GEN_DIV="Z(E, M) ...")
  *
  * For each X format and rounding mode R (bit 0 toward zero, bit 1 flush to
  * zero) it prints GenCircuit<E, M, R, OPC>
  * specialisations for the op classes add (b's sign flip is applied by the
  * caller), mul, fma2 and div, with eval(a, b, c, r) over the B slices of each
  * operand.  For each Y format it prints add and mul under RN and RZ only (the
- * kernels compose fma2 from those two).  The printed file is included inside
+ * kernels compose fma2 from those two), and for each Z format div under RN
+ * and RZ.  The printed file is included inside
  * namespace bsfp by gen_circuit.cuh, which defines BSFP_LOP3 and
  * BSFP_GEN_FN.
  */
@@ -34,14 +36,17 @@
 
 #include "netlist.h"
 
-#if !defined(BSFP_GEN_FORMATS) && !defined(BSFP_GEN_ADDMUL)
-#error "compile with -DBSFP_GEN_FORMATS=\"X(E, M) ...\" and/or -DBSFP_GEN_ADDMUL=\"Y(E, M) ...\""
+#if !defined(BSFP_GEN_FORMATS) && !defined(BSFP_GEN_ADDMUL) && !defined(BSFP_GEN_DIV)
+#error "compile with -DBSFP_GEN_FORMATS=\"X(E, M) ...\", -DBSFP_GEN_ADDMUL=\"Y(E, M) ...\" or -DBSFP_GEN_DIV=\"Z(E, M) ...\""
 #endif
 #ifndef BSFP_GEN_FORMATS
 #define BSFP_GEN_FORMATS
 #endif
 #ifndef BSFP_GEN_ADDMUL
 #define BSFP_GEN_ADDMUL
+#endif
+#ifndef BSFP_GEN_DIV
+#define BSFP_GEN_DIV
 #endif
 
 namespace bsfp {
@@ -126,6 +131,13 @@ void emit_addmul(FILE* f) {
     emit<E, M, 1, OP_MUL>(f, 1);
 }
 
+/* div, RN and RZ */
+template <int E, int M>
+void emit_div(FILE* f) {
+    emit<E, M, 0, OP_DIV>(f, 3);
+    emit<E, M, 1, OP_DIV>(f, 3);
+}
+
 }  // namespace
 }  // namespace gc
 }  // namespace bsfp
@@ -148,6 +160,9 @@ int main(int argc, char** argv) {
 #define Y(E, M) bsfp::gc::emit_addmul<E, M>(f);
     BSFP_GEN_ADDMUL
 #undef Y
+#define Z(E, M) bsfp::gc::emit_div<E, M>(f);
+    BSFP_GEN_DIV
+#undef Z
     if (fclose(f) != 0) {
         perror(argv[1]);
         return 1;

@@ -9,8 +9,8 @@
  * The specialisations come from gen_circuits.cuh, which circuitgen writes at
  * build time for the formats the build lists (every op and mode), and from
  * the header of the translation unit's part (add and mul under RN and RZ of
- * every other format); where `available` is false the kernels use the
- * templates.
+ * every other format, or, in a division unit, div under RN and RZ); where
+ * `available` is false the kernels use the templates.
  *
  * Device code emits lop3.b32 through inline PTX, which the compiler keeps as
  * one instruction; host code evaluates the same truth tables bitwise (used by
@@ -53,8 +53,8 @@ inline uint32_t lop3_gate(uint32_t a, uint32_t b, uint32_t c) {
 
 #if defined(BSFP_HAVE_GEN)
 #include "gen_circuits.cuh"
-/* add and mul (RN, RZ) of the other formats of one element-wise translation
- * unit, whose build names its header */
+/* add and mul (or div) under RN and RZ of the other formats of one
+ * element-wise translation unit, whose build names its header */
 #if defined(BSFP_GEN_PART)
 #include BSFP_GEN_PART
 #endif
