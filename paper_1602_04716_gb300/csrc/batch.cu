@@ -331,9 +331,14 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
         return set_cuda_error(err);
     }
     bsfp_status st = BSFP_OK;
-    /* side streams and events for the streamed groups' parallel branches */
+    /* side streams and events for the plan's parallel branches */
     constexpr int NBRANCH = 8;
-    const size_t nbranches = sgroups.size() + (udesc[0].empty() ? 0 : 1) + (udesc[1].empty() ? 0 : 1);
+    bool any_plain = false;
+    for (int32_t i = 0; i < njobs; ++i) any_plain = any_plain || (group[(size_t)i] < 0 && !prep[(size_t)i].skip);
+    size_t npersistent = 0;
+    for (int g = 0; g < OPC_COUNT; ++g) npersistent += tmap[g].empty() ? 0 : 1;
+    const size_t nbranches = sgroups.size() + (udesc[0].empty() ? 0 : 1) + (udesc[1].empty() ? 0 : 1) + npersistent +
+                             (any_plain ? 1 : 0);
     const int nside = (int)(nbranches < (size_t)NBRANCH ? nbranches : (size_t)NBRANCH);
     cudaStream_t side[NBRANCH] = {};
     cudaEvent_t fork = nullptr, join[NBRANCH] = {};
@@ -344,11 +349,13 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
     if (err == cudaSuccess && nside) err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
-        /* streamed groups: one block per SM, at most one per tile.  The
-         * groups are independent, so they are captured as parallel branches
-         * (group g on side stream g mod 8): one group's blocks take the SMs
+        /* Every kernel of the plan is independent of the others, so each
+         * group -- a unified or streamed group, a persistent op class, and
+         * the plain launches together -- is captured as a parallel branch
+         * (branch b on side stream b mod 8): one group's blocks take the SMs
          * that another's last tiles leave idle, instead of each launch
-         * ramping up and draining on its own. */
+         * ramping up and draining on its own.  Streamed groups run one block
+         * per SM, at most one per tile. */
         if (nside) {
             cudaError_t e2 = cudaEventRecord(fork, cs);
             for (int i = 0; i < nside && e2 == cudaSuccess; ++i) e2 = cudaStreamWaitEvent(side[i], fork, 0);
@@ -370,6 +377,19 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
             if (e2 != cudaSuccess) st = set_cuda_error(e2);
             else p->launches += 1;
         }
+        /* then the persistent kernels, one branch per op class */
+        for (int g = 0; g < OPC_COUNT && st == BSFP_OK; ++g) {
+            if (tmap[g].empty()) continue;
+            cudaStream_t bs = side[branch++ % NBRANCH];
+            unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + off_cnt[g]);
+            cudaError_t e2 = cudaMemsetAsync(cnt, 0, sizeof *cnt, bs);
+            if (e2 == cudaSuccess)
+                e2 = batch_launcher(g, o.wpt)(reinterpret_cast<const JobDesc*>(base + off_desc[g]),
+                                              reinterpret_cast<const int32_t*>(base + off_map[g]),
+                                              (int64_t)tmap[g].size(), cnt, grid[g], bs);
+            if (e2 != cudaSuccess) st = set_cuda_error(e2);
+            else p->launches += 1;
+        }
         for (size_t g = 0; g < sgroups.size() && st == BSFP_OK; ++g) {
             const int64_t ntiles = (int64_t)sgroups[g].tmap.size();
             const int64_t sms = device_num_sms();
@@ -380,28 +400,21 @@ bsfp_status bsfp_batch_plan_create(const bsfp_job* jobs, int32_t njobs, const bs
             if (e2 != cudaSuccess) st = set_cuda_error(e2);
             else p->launches += 1;
         }
+        /* the plain launches, one after another on one branch */
+        if (any_plain && st == BSFP_OK) {
+            cudaStream_t bs = side[branch++ % NBRANCH];
+            for (int32_t i = 0; i < njobs && st == BSFP_OK; ++i) {
+                if (group[(size_t)i] >= 0 || prep[(size_t)i].skip) continue;
+                st = launch_prepared(prep[(size_t)i], bs);
+                if (st == BSFP_OK) p->launches += 1;
+            }
+        }
         /* join every branch back (also after an error: the capture must end
          * with all its streams joined) */
         for (int i = 0; i < nside; ++i) {
             cudaError_t e2 = cudaEventRecord(join[i], side[i]);
             if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, join[i], 0);
             if (e2 != cudaSuccess && st == BSFP_OK) st = set_cuda_error(e2);
-        }
-        for (int g = 0; g < OPC_COUNT && st == BSFP_OK; ++g) {
-            if (tmap[g].empty()) continue;
-            unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + off_cnt[g]);
-            cudaError_t e2 = cudaMemsetAsync(cnt, 0, sizeof *cnt, cs);
-            if (e2 == cudaSuccess)
-                e2 = batch_launcher(g, o.wpt)(reinterpret_cast<const JobDesc*>(base + off_desc[g]),
-                                              reinterpret_cast<const int32_t*>(base + off_map[g]),
-                                              (int64_t)tmap[g].size(), cnt, grid[g], cs);
-            if (e2 != cudaSuccess) st = set_cuda_error(e2);
-            else p->launches += 1;
-        }
-        for (int32_t i = 0; i < njobs && st == BSFP_OK; ++i) {
-            if (group[(size_t)i] >= 0 || prep[(size_t)i].skip) continue;
-            st = launch_prepared(prep[(size_t)i], cs);
-            if (st == BSFP_OK) p->launches += 1;
         }
         cudaGraph_t g = nullptr;
         const cudaError_t e3 = cudaStreamEndCapture(cs, &g);
