@@ -84,9 +84,13 @@ def _units():
         units.append(("stream_e%d_m%d.o" % (e, m), cu + ["-DBSFP_SE=%d" % e, "-DBSFP_SM=%d" % m,
                                                          os.path.join(CSRC, "stream_inst.cu")]))
     for e in range(2, 9):
-        # the printed netlists of this exponent width's formats (both parts)
-        units.append(("stream_mul_e%d.o" % e, cu + ["-DBSFP_SE=%d" % e, "-DBSFP_GEN_PART=\"gen_e%d_all.cuh\"" % e,
-                                                    os.path.join(CSRC, "stream_mul_inst.cu")]))
+        # streamed mul, fma2 and division of the other formats, each with the printed netlists of
+        # this exponent width's formats (both parts)
+        for op, opc, hdr in (("mul", 1, "gen_e%d_all.cuh"), ("fma2", 2, "gen_e%d_all.cuh"),
+                             ("div", 3, "gen_div_e%d_all.cuh")):
+            units.append(("stream_%s_e%d.o" % (op, e),
+                          cu + ["-DBSFP_SE=%d" % e, "-DBSFP_SOPC=%d" % opc, "-DBSFP_GEN_PART=\"%s\"" % (hdr % e),
+                                os.path.join(CSRC, "stream_band_inst.cu")]))
     for opc in range(3):
         units.append(("batch_opc%d.o" % opc, cu + ["-DBSFP_BATCH_OPC=%d" % opc, os.path.join(CSRC, "batch_inst.cu")]))
     for opc in range(2):
@@ -135,10 +139,11 @@ def generate(jobs: int | None = None) -> str:
                         fh.write("/* no formats of this part need printed netlists */\n")
     for e in range(2, 9):
         # both parts of an exponent width, for the units that span every fraction width
-        path = os.path.join(GEN_DIR, "gen_e%d_all.cuh" % e)
-        if not os.path.exists(path) or os.path.getmtime(path) < newest:
-            with open(path, "w") as fh:
-                fh.write("".join('#include "%s"\n' % part_header(e, lo) for lo, _ in M_RANGES))
+        for name, hdr in (("gen_e%d_all.cuh", part_header), ("gen_div_e%d_all.cuh", div_header)):
+            path = os.path.join(GEN_DIR, name % e)
+            if not os.path.exists(path) or os.path.getmtime(path) < newest:
+                with open(path, "w") as fh:
+                    fh.write("".join('#include "%s"\n' % hdr(e, lo) for lo, _ in M_RANGES))
     todo = [t for t in todo if not os.path.exists(t[1]) or os.path.getmtime(t[1]) < newest]
     with ThreadPoolExecutor(jobs or max(1, os.cpu_count() or 1)) as ex:
         for fut in [ex.submit(_generate_one, *t) for t in todo]:

@@ -44,11 +44,18 @@ void register_int_w1(); void register_int_w17();
 /* streamed kernels, one translation unit per format (stream_inst.cu) */
 void register_stream_e4_m3(); void register_stream_e4_m4(); void register_stream_e5_m7();
 void register_stream_e5_m10(); void register_stream_e8_m7();
-/* streamed mul of the other formats of 12..24 planes, one unit per exponent
- * width (stream_mul_inst.cu) */
+/* streamed mul (12..24 planes), fma2 (10..17) and division (8..17) of the
+ * other formats, one unit per exponent width and op class
+ * (stream_band_inst.cu) */
 void register_stream_mul_e2(); void register_stream_mul_e3(); void register_stream_mul_e4();
 void register_stream_mul_e5(); void register_stream_mul_e6(); void register_stream_mul_e7();
 void register_stream_mul_e8();
+void register_stream_div_e2(); void register_stream_div_e3(); void register_stream_div_e4();
+void register_stream_div_e5(); void register_stream_div_e6(); void register_stream_div_e7();
+void register_stream_div_e8();
+void register_stream_fma2_e2(); void register_stream_fma2_e3(); void register_stream_fma2_e4();
+void register_stream_fma2_e5(); void register_stream_fma2_e6(); void register_stream_fma2_e7();
+void register_stream_fma2_e8();
 
 cudaError_t launch_pack(int cb, const void* in, int64_t n, int B, uint32_t* out, int64_t S, cudaStream_t st);
 cudaError_t launch_unpack(int cb, const uint32_t* in, int64_t S, int B, void* out, int64_t n, cudaStream_t st);
@@ -77,6 +84,10 @@ static void init_tables() {
     register_stream_e5_m10(); register_stream_e8_m7();
     register_stream_mul_e2(); register_stream_mul_e3(); register_stream_mul_e4(); register_stream_mul_e5();
     register_stream_mul_e6(); register_stream_mul_e7(); register_stream_mul_e8();
+    register_stream_div_e2(); register_stream_div_e3(); register_stream_div_e4(); register_stream_div_e5();
+    register_stream_div_e6(); register_stream_div_e7(); register_stream_div_e8();
+    register_stream_fma2_e2(); register_stream_fma2_e3(); register_stream_fma2_e4(); register_stream_fma2_e5();
+    register_stream_fma2_e6(); register_stream_fma2_e7(); register_stream_fma2_e8();
 }
 
 /* The streamed kernel is taken only when every SM gets at least this many

@@ -110,6 +110,24 @@ __device__ __forceinline__ void column_op(uint32_t* x, uint32_t* y, const uint32
     }
 }
 
+/* The B result slices of WPT word columns starting at w0 (a multiple of
+ * WPT) to the output planes.  Masked tail: the partly filled column keeps
+ * only its valid lanes and padding columns become zero. */
+template <int B, int WPT>
+__device__ __forceinline__ void masked_store(const BinopArgs& p, int64_t w0, uint32_t (*r)[WPT]) {
+    if (w0 + WPT >= p.nwords) {
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            const int64_t w = w0 + k;
+            const uint32_t m = (w + 1 < p.nwords) ? ~0u : (w + 1 == p.nwords ? p.tailmask : 0u);
+#pragma unroll
+            for (int i = 0; i < B; ++i) r[i][k] &= m;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) vstore<WPT>(p.out + i * p.S + w0, r[i]);
+}
+
 /* The circuit on WPT word columns starting at w0 (a multiple of WPT) whose
  * input slices are already in registers, then the masked stores. */
 template <int E, int M, int R, int OPC, int WPT>
@@ -130,19 +148,7 @@ __device__ __forceinline__ void binop_compute_store(const BinopArgs& p, int64_t 
 #pragma unroll
         for (int i = 0; i < B; ++i) r[i][k] = o[i];
     }
-    /* masked tail: the partly filled column keeps only its valid lanes and
-     * padding columns become zero */
-    if (w0 + WPT >= p.nwords) {
-#pragma unroll
-        for (int k = 0; k < WPT; ++k) {
-            const int64_t w = w0 + k;
-            const uint32_t m = (w + 1 < p.nwords) ? ~0u : (w + 1 == p.nwords ? p.tailmask : 0u);
-#pragma unroll
-            for (int i = 0; i < B; ++i) r[i][k] &= m;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < B; ++i) vstore<WPT>(p.out + i * p.S + w0, r[i]);
+    masked_store<B, WPT>(p, w0, r);
 }
 
 /* WPT word columns starting at w0 (a multiple of WPT). */

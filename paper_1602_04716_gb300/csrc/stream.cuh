@@ -42,17 +42,31 @@
 
 namespace bsfp {
 
-/* Formats and op classes compiled with a streamed kernel: the tuned formats
- * of at most 16 planes (add/sub and mul, every mode, and their job-list
- * form), and mul under RN and RZ of every other format of 12 to 24 planes
- * (stream_mul_inst.cu) -- the band where the multiplier sits near the
- * crossover of logic and HBM bounds and the grid-stride kernel, with few
- * warps resident, leaves both pipes idle part of the time. */
+/* Formats and op classes compiled with a streamed kernel:
+ *   the tuned formats of at most 16 planes: add/sub and mul, every mode, and
+ *     their job-list form; division and fma2, every mode, where their bands
+ *     below include the format (stream_inst.cu);
+ *   every other format, RN and RZ (stream_band_inst.cu): mul of 12 to 24
+ *     planes -- the band where the multiplier sits near the crossover of
+ *     logic and HBM bounds and the grid-stride kernel, with few warps
+ *     resident, leaves both pipes idle part of the time; division of 8 to 17
+ *     planes with at least 3 fraction bits, where the same holds: the divider
+ *     needs 64-128 registers a thread in the grid-stride kernel (4-8 warps
+ *     per scheduler), while with 2 fraction bits it is light and HBM-bound
+ *     and the grid-stride kernel was faster; fma2 of 10 to 19 planes with
+ *     at least 4 fraction bits, bound by the logic pipe from about 11 planes
+ *     on, whose grid-stride kernel holds all 3B input slices while the
+ *     multiplier runs (with fewer fraction bits the multiplier is light, the
+ *     op HBM-bound, and the grid-stride kernel was faster). */
 constexpr bool stream_format(int E, int M) { return tuned_format(E, M) && 1 + E + M <= 16; }
-constexpr bool stream_mul_format(int E, int M) {
-    return !tuned_format(E, M) && 1 + E + M >= 12 && 1 + E + M <= 24;
+constexpr bool stream_div_format(int E, int M) { return 1 + E + M >= 8 && 1 + E + M <= 17 && M >= 3; }
+constexpr bool stream_fma2_format(int E, int M) { return 1 + E + M >= 10 && 1 + E + M <= 19 && M >= 4; }
+constexpr bool stream_band_format(int E, int M, int opc) {
+    return opc == OPC_MUL    ? (1 + E + M >= 12 && 1 + E + M <= 24)
+         : opc == OPC_DIV    ? stream_div_format(E, M)
+         : opc == OPC_FMA2   ? stream_fma2_format(E, M)
+                             : false;
 }
-constexpr bool stream_opc(int opc) { return opc == OPC_ADDSUB || opc == OPC_MUL; }
 
 template <int E, int M, int OPC>
 struct StreamShape {
@@ -67,11 +81,25 @@ struct StreamShape {
      * Wider formats: 8 x 2 up to 24 planes, 6 x 2 beyond, so that the ring
      * of 2B planes fits and each thread may hold the wide multipliers'
      * registers. */
-    static constexpr int NC = B <= 9 ? 11
+    static constexpr int NC_ADDMUL = B <= 9 ? 11
                             : (B <= 13 ? (OPC == OPC_ADDSUB ? 11 : 15)
                                        : (B <= 16 ? ((OPC == OPC_MUL && E == 8) ? 14 : 12) : (B <= 24 ? 8 : 6)));
-    static constexpr int NST = B <= 9 ? 4 : ((B <= 13 && OPC == OPC_ADDSUB) ? 3 : 2);   /* ring stages */
-    static constexpr int NIN = 2 * B;                               /* input planes per tile */
+    /* division (8 to 17 planes): 15 x 2 up to 13 planes, 12 x 2 beyond,
+     * each faster than 11 x 3, 8 x 3 and the one-word-per-thread shapes on
+     * 2^27-element operands.  fma2 (10 to 19 planes): 11 x 2 with the
+     * addend's planes in the ring up to 13 planes; 12 x 2 beyond, where the
+     * ring holds only a and b and the consumers load the addend from global
+     * memory once the product is done (3B planes of 12 warps' tiles would
+     * not fit).  Both were 9-14% faster than the grid-stride kernel on nine
+     * formats at 2^27 elements; 15 x 2, 15 x 3 and 12 x 2 at one word per
+     * thread, and 10 x 2, were slower.  18 and 19 planes take 11 x 2 with
+     * the addend from global memory, so that 2B planes still fit. */
+    static constexpr int NC_FMA2 = B <= 13 ? 11 : (B <= 17 ? 12 : 11);
+    static constexpr int NC = OPC == OPC_DIV ? (B <= 13 ? 15 : 12) : (OPC == OPC_FMA2 ? NC_FMA2 : NC_ADDMUL);
+    static constexpr int NST = (OPC == OPC_DIV || OPC == OPC_FMA2) ? 2
+                             : (B <= 9 ? 4 : ((B <= 13 && OPC == OPC_ADDSUB) ? 3 : 2));   /* ring stages */
+    static constexpr bool Z_IN_RING = OPC == OPC_FMA2 && B <= 13;   /* fma2: the addend's planes in the ring */
+    static constexpr int NIN = (Z_IN_RING ? 3 : 2) * B;             /* input planes per tile */
     static constexpr int TW = 32 * NC * WPT;                        /* words per plane per tile */
     static constexpr int THREADS = 32 * (NC + 1);
     static constexpr int HDR = 128;                                 /* barriers */
@@ -80,6 +108,60 @@ struct StreamShape {
     static_assert(SMEM <= 232448, "ring fits the shared memory one block may opt in to");
     static_assert((size_t)NIN * TW * 4 < (1u << 20), "a stage's bytes fit the transaction count");
 };
+
+/* One fma2 tile column pair of a consumer thread: the product of its a and b
+ * slices (rounded once, kept in registers), then the addend's slices -- from
+ * the ring when the shape holds them there, else from global memory -- and
+ * the sum (rounded again): fma2 = round(round(a*b) + c).  The stage
+ * is released once the thread has read everything it needs from it.  Reading
+ * the addend only after the product keeps its B slices out of the registers
+ * the multiplier needs. */
+template <int E, int M, int R, class SH>
+__device__ __forceinline__ void stream_fma2_tile(const BinopArgs& p, const uint32_t* src, int64_t w0, int lane,
+                                                 uint32_t empty_bar) {
+    constexpr int B = SH::B, TW = SH::TW, WPT = SH::WPT;
+    uint32_t pr[B][WPT], z[B][WPT];
+#pragma unroll
+    for (int w = 0; w < WPT; ++w) {
+        uint32_t x[B], y[B], o[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            x[i] = src[i * TW + w];
+            y[i] = src[(B + i) * TW + w];
+        }
+        column_op<E, M, R, OPC_MUL>(x, y, y, o, 0u);
+#pragma unroll
+        for (int i = 0; i < B; ++i) pr[i][w] = o[i];
+    }
+    if constexpr (SH::Z_IN_RING) {
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int w = 0; w < WPT; ++w) z[i][w] = src[(2 * B + i) * TW + w];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty_bar);
+    /* S is a multiple of 32, so a pair of columns is all in or all out */
+    if (w0 >= p.S) return;
+    if constexpr (!SH::Z_IN_RING) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) vload<WPT>(p.c + i * p.S + w0, z[i]);
+    }
+    uint32_t r[B][WPT];
+#pragma unroll
+    for (int w = 0; w < WPT; ++w) {
+        uint32_t x[B], y[B], o[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            x[i] = pr[i][w];
+            y[i] = z[i][w];
+        }
+        column_op<E, M, R, OPC_ADDSUB>(x, y, y, o, 0u);
+#pragma unroll
+        for (int i = 0; i < B; ++i) r[i][w] = o[i];
+    }
+    masked_store<B, WPT>(p, w0, r);
+}
 
 /* The bound is on threads only: the block size alone caps registers at
  * 65536 / THREADS.  Adding a minimum of one block per SM changes ptxas's
@@ -122,7 +204,8 @@ __global__ void __launch_bounds__(StreamShape<E, M, OPC>::THREADS) stream_kernel
                 const uint32_t dst = smem_addr(ring + (size_t)s * NIN * TW);
 #pragma unroll 1
                 for (int q = 0; q < NIN; ++q) {
-                    const uint32_t* src = (q < B) ? p.a + (int64_t)q * p.S : p.b + (int64_t)(q - B) * p.S;
+                    const uint32_t* src = (q < B) ? p.a + (int64_t)q * p.S
+                                        : (q < 2 * B ? p.b + (int64_t)(q - B) * p.S : p.c + (int64_t)(q - 2 * B) * p.S);
                     bulk_copy_g2s(dst + (uint32_t)(q * TW * 4), src + t * TW, bytes, bar);
                 }
             }
@@ -144,6 +227,10 @@ __global__ void __launch_bounds__(StreamShape<E, M, OPC>::THREADS) stream_kernel
         const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)((k / NST) & 1), ab, p.wait_cycles);
         if (!__all_sync(0xFFFFFFFFu, ok)) break;   /* the warp leaves together */
         const uint32_t* src = ring + (size_t)s * NIN * TW + j0;
+        if constexpr (OPC == OPC_FMA2) {
+            stream_fma2_tile<E, M, R, SH>(p, src, t * TW + j0, lane, smem_addr(&empty[s]));
+            continue;
+        }
         uint32_t xa[B][WPT], xb[B][WPT], xc[1][WPT];
 #pragma unroll
         for (int i = 0; i < B; ++i) {

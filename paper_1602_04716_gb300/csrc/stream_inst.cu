@@ -1,8 +1,10 @@
 /*
  * stream_inst.cu -- instantiates the streamed kernels (stream.cuh) for one
  * format, compiled once per format with -DBSFP_SE=E -DBSFP_SM=M, and adds
- * them to that format's dispatch-table entries (add/sub and mul, every
- * rounding mode) as variant VARIANT_STREAMED.  Registered after the
+ * them to that format's dispatch-table entries (add/sub and mul with their
+ * job-list form, and division and fma2 where the format lies in their
+ * bands, every rounding mode) as variant VARIANT_STREAMED.  Which variant a call takes
+ * stays the autotuner's choice for these formats.  Registered after the
  * grid-stride kernels, whose entries it extends.
  */
 #include "stream.cuh"
@@ -26,10 +28,23 @@ static void add_stream(BinopEntry& e) {
     e.wpt_mask |= (unsigned)VARIANT_STREAMED;
 }
 
+/* division and fma2 run their streamed kernel only as single calls: no
+ * job-list form */
+template <int E, int M, int R, int OPC>
+static void add_stream_single(BinopEntry& e) {
+    e.stream_launch = stream_launch<E, M, R, OPC>;
+    e.stream_prepare = stream_prepare<E, M, R, OPC>;
+    e.stream_tw = StreamShape<E, M, OPC>::TW;
+    e.stream_nst = StreamShape<E, M, OPC>::NST;
+    e.wpt_mask |= (unsigned)VARIANT_STREAMED;
+}
+
 template <int E, int M, int R>
 static void fill_stream_mode() {
     add_stream<E, M, R, OPC_ADDSUB>(g_binop_table[E][M][R][OPC_ADDSUB]);
     add_stream<E, M, R, OPC_MUL>(g_binop_table[E][M][R][OPC_MUL]);
+    if constexpr (stream_div_format(E, M)) add_stream_single<E, M, R, OPC_DIV>(g_binop_table[E][M][R][OPC_DIV]);
+    if constexpr (stream_fma2_format(E, M)) add_stream_single<E, M, R, OPC_FMA2>(g_binop_table[E][M][R][OPC_FMA2]);
 }
 
 #define BSFP_SCAT2(a, b) a##b

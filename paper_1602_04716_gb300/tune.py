@@ -152,7 +152,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=1 << 28, help="elements per operand (the at-scale size)")
     ap.add_argument("--out", default=CACHE)
     ap.add_argument("--band-n", type=int, default=1 << 26,
-                    help="elements per operand when choosing the streamed mul of the other formats")
+                    help="elements per operand when choosing the streamed mul, fma2 and division of the other formats")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     for E, M in TUNED_FORMATS:
@@ -168,22 +168,27 @@ def main(argv=None):
                                                                         op, best[0], best[1], table[best]), flush=True)
             del a, b, c, o
             torch.cuda.empty_cache()
-    # mul of the other formats that have a streamed kernel (12..24 planes): the grid-stride default
-    # against the streamed kernel, per format and rounding, at the sweep's size
+    # mul (12..24 planes), fma2 (10..17) and division (8..17) of the other formats that have a
+    # streamed kernel: the grid-stride default against the streamed kernel, per format and rounding,
+    # at the sweep's size
     for E in range(2, 9):
         for M in range(1, 24):
             if (E, M) in TUNED_FORMATS or 1 + E + M > 32:
                 continue
             for rnd in (_b.RN, _b.RZ):
                 f = _b.Format(E, M, rnd)
-                if _b.VARIANT_STREAMED not in _b.bsfp_variants_compiled(f, "mul"):
+                ops = [op for op in ("mul", "fma2", "div")
+                       if _b.VARIANT_STREAMED in _b.bsfp_variants_compiled(f, op)]
+                if not ops:
                     continue
-                a, b = (torch.zeros(f.bits * _b.bsfp_plane_stride(args.band_n), dtype=torch.int32, device="cuda")
-                        for _ in range(2))
+                a, b, c = (torch.zeros(f.bits * _b.bsfp_plane_stride(args.band_n), dtype=torch.int32,
+                                       device="cuda") for _ in range(3))
                 o = _b.empty_bitslice(f, args.band_n)
-                best, table = autotune("mul", f, a, b, None, o, args.band_n, bps_choices=(0,), path=args.out)
-                print("1/%d/%d %s mul: wpt %d (%.3f ms)" % (E, M, ("RN", "RZ")[rnd], best[0], table[best]), flush=True)
-                del a, b, o
+                for op in ops:
+                    best, table = autotune(op, f, a, b, c, o, args.band_n, bps_choices=(0,), path=args.out)
+                    print("1/%d/%d %s %s: wpt %d (%.3f ms)" % (E, M, ("RN", "RZ")[rnd], op, best[0], table[best]),
+                          flush=True)
+                del a, b, c, o
     torch.cuda.empty_cache()
     # the batched kernels on a mixed workload of the five batched formats
     import numpy as np

@@ -116,7 +116,8 @@ def test_variants_and_overrides():
     f = bs.Format(5, 7)
     assert bs.bsfp_variants_compiled(f, "add") == [1, 2, 4, bs.VARIANT_STREAMED]
     assert bs.bsfp_variants_compiled(f, "mul") == [1, 2, 4, bs.VARIANT_STREAMED]
-    assert bs.bsfp_variants_compiled(f, "fma2") == [1, 2]
+    assert bs.bsfp_variants_compiled(f, "fma2") == [1, 2, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variants_compiled(bs.Format(4, 4), "fma2") == [1, 2, 4]   # 9 planes: below the fma2 band
     assert bs.bsfp_variants_compiled(bs.Format(8, 23), "mul") == [1, 2]
     assert bs.bsfp_variant(f, "add") in (1, 2, 4, bs.VARIANT_STREAMED)
     g = bs.Format(6, 9)
@@ -126,6 +127,26 @@ def test_variants_and_overrides():
     assert bs.bsfp_variant(g, "mul") == bs.VARIANT_STREAMED
     assert len(bs.bsfp_variants_compiled(g, "add")) == 1
     assert bs.bsfp_variants_compiled(bs.Format(3, 5), "mul") == [2]   # 9 planes: below the streamed band
+    # division: streamed for 8..17 planes and 3 fraction bits or more, the default for the formats
+    # outside the tuned set from 4 fraction bits on
+    assert bs.bsfp_variants_compiled(f, "div") == [1, 2, 4, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variants_compiled(g, "div") == [2, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variant(g, "div") == bs.VARIANT_STREAMED
+    assert bs.bsfp_variants_compiled(bs.Format(3, 5), "div") == [2, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variants_compiled(bs.Format(7, 10), "div") == [2]   # 18 planes: above the band
+    assert bs.bsfp_variants_compiled(bs.Format(3, 2), "div") == [2]    # 6 planes: below it
+    assert bs.bsfp_variants_compiled(bs.Format(6, 2), "div") == [2]    # 2 fraction bits: HBM-bound, none
+    # fma2: streamed for 10..19 planes and 4 fraction bits or more, the default for the formats outside
+    # the tuned set
+    assert bs.bsfp_variants_compiled(g, "fma2") == [1, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variant(g, "fma2") == bs.VARIANT_STREAMED
+    assert bs.bsfp_variants_compiled(bs.Format(3, 6), "fma2") == [2, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variants_compiled(bs.Format(8, 10), "fma2") == [1, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variants_compiled(bs.Format(3, 5), "fma2") == [2]   # 9 planes: below the band
+    assert bs.bsfp_variants_compiled(bs.Format(8, 11), "fma2") == [1]  # 20 planes: above it
+    assert bs.bsfp_variants_compiled(bs.Format(8, 3), "fma2") == [2]   # 3 fraction bits: HBM-bound, none
+    assert bs.bsfp_variants_compiled(bs.Format(6, 3), "div") == [2, bs.VARIANT_STREAMED]
+    assert bs.bsfp_variant(bs.Format(6, 3), "div") in (2, bs.VARIANT_STREAMED)   # 3 bits: the tuner's choice
     with pytest.raises(bs.BsfpError):
         bs.bsfp_set_variant(g, "mul", 4)
     bs.bsfp_set_variant(f, "mul", 1, 3)
@@ -133,7 +154,7 @@ def test_variants_and_overrides():
     bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED, 0)
     assert bs.bsfp_variant(f, "mul") == bs.VARIANT_STREAMED
     with pytest.raises(bs.BsfpError):
-        bs.bsfp_set_variant(f, "fma2", bs.VARIANT_STREAMED)
+        bs.bsfp_set_variant(bs.Format(4, 4), "fma2", bs.VARIANT_STREAMED)
     for bad in (3, 5, 16):
         with pytest.raises(bs.BsfpError):
             bs.bsfp_set_variant(f, "mul", bad)
@@ -304,8 +325,15 @@ def test_stream_shape_query():
     assert bs.bsfp_stream_shape(bs.Format(5, 7), "mul") == (32 * 15 * 2, 2)
     assert bs.bsfp_stream_shape(bs.Format(4, 4, bs.RZ), "mul") == (32 * 11 * 2, 4)
     assert bs.bsfp_stream_shape(bs.Format(8, 7), "mul") == (32 * 14 * 2, 2)
-    for f, op in ((bs.Format(5, 7), "fma2"), (bs.Format(5, 7), "div"), (bs.Format(3, 5), "add"),
-                  (bs.Format(8, 23), "mul")):
+    assert bs.bsfp_stream_shape(bs.Format(5, 7), "div") == (32 * 15 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(3, 5, bs.RZ), "div") == (32 * 15 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(7, 9), "div") == (32 * 12 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(5, 7), "fma2") == (32 * 11 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(8, 7, bs.RZ_FTZ), "fma2") == (32 * 12 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(6, 9), "fma2") == (32 * 12 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(8, 10), "fma2") == (32 * 11 * 2, 2)
+    for f, op in ((bs.Format(4, 4), "fma2"), (bs.Format(8, 11), "fma2"), (bs.Format(3, 5), "add"),
+                  (bs.Format(8, 23), "mul"), (bs.Format(8, 23), "div"), (bs.Format(3, 5, bs.RN_FTZ), "div")):
         with pytest.raises(bs.BsfpError) as ei:
             bs.bsfp_stream_shape(f, op)
         assert ei.value.status == bs.ERR_UNSUPPORTED

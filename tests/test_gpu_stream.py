@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 
 STREAM_FORMATS = [(4, 3), (4, 4), (5, 7), (5, 10), (8, 7)]
 MODES = [oracle.RN, oracle.RZ, oracle.RN_FTZ, oracle.RZ_FTZ]
-OPS = ["add", "sub", "mul"]
+OPS = ["add", "sub", "mul", "div"]
 
 
 def shape(E, M, op="add"):
@@ -44,7 +44,7 @@ def _cuda():
     torch.cuda.synchronize()
     for E, M in STREAM_FORMATS:
         for rnd in MODES:
-            for op in OPS:
+            for op in OPS + ["fma2"]:
                 bs.bsfp_set_variant(bs.Format(E, M, rnd), op, 0, 0)
 
 
@@ -60,12 +60,15 @@ def test_streamed_variant_is_compiled_where_documented():
             f = bs.Format(E, M, rnd)
             for op in OPS:
                 assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(f, op), (E, M, rnd, op)
-            for op in ("fma2", "div"):
-                assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(f, op)
+            assert (bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(f, "fma2")) == (1 + E + M >= 10)
     for E, M in [(8, 23), (3, 2)]:
-        assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(bs.Format(E, M), "mul")
-    # outside the tuned set: the streamed mul (RN, RZ) for 12..24 planes, no streamed add
+        for op in ("mul", "fma2", "div"):
+            assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(bs.Format(E, M), op)
+    # outside the tuned set (RN, RZ): the streamed mul for 12..24 planes, fma2 for 10..19 and division
+    # for 8..17, no streamed add
     assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(6, 9, 1), "mul")
+    assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(6, 9, 1), "fma2")
+    assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(6, 9, 1), "div")
     assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(bs.Format(6, 9), "add")
     with pytest.raises(bs.BsfpError):
         bs.bsfp_set_variant(bs.Format(6, 9), "add", bs.VARIANT_STREAMED)
@@ -106,7 +109,7 @@ def test_several_rounds_of_the_ring(E, M):
     with the oracle, in all four modes."""
     B = 1 + E + M
     # every op class gets NST + 2 tiles per block or more
-    TW, NST = max((shape(E, M, op) for op in ("add", "mul")), key=lambda s: s[0] * (s[1] + 2))
+    TW, NST = max((shape(E, M, op) for op in ("add", "mul", "div")), key=lambda s: s[0] * (s[1] + 2))
     n = bs.bsfp_num_sms() * (NST + 2) * 32 * TW - 3 * 32 * TW // 2 + 12345
     cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[bs.bsfp_container_bytes(bs.Format(E, M))]
     std = bs.empty_standard(bs.Format(E, M), n)
@@ -137,6 +140,72 @@ def test_several_rounds_of_the_ring(E, M):
             want = oracle.binop(op, E, M, rnd, xa, xb)
             bad = np.nonzero(res != want)[0]
             assert not len(bad), "%s 1/%d/%d rnd=%d: %d bad, first idx %d" % (op, E, M, rnd, len(bad), idx[bad[0]])
+    assert bs.bsfp_fault_status() == 0
+    del planes, ref, got, std
+    torch.cuda.empty_cache()
+
+
+FMA2_STREAM_FORMATS = [(E, M) for E, M in STREAM_FORMATS if 1 + E + M >= 10]
+
+
+@pytest.mark.parametrize("E,M", FMA2_STREAM_FORMATS)
+@pytest.mark.parametrize("rnd", MODES)
+def test_streamed_fma2_tile_geometry_vs_oracle(E, M, rnd):
+    """The streamed fma2 (product first, then the addend: from the ring up to
+    13 planes, from global memory beyond) at the tile-geometry sizes, every
+    word of the output planes against the oracle, in all four modes."""
+    B = 1 + E + M
+    f = bs.Format(E, M, rnd)
+    TW, _ = shape(E, M, "fma2")
+    for n in (1, 33, 32 * TW - 1, 32 * TW + 1, 3 * 32 * TW + 77):
+        a, b, c = (synth.fp_values(E, M, n, seed + n % 7).astype(np.uint32) for seed in (811, 822, 833))
+        pa, pb, pc = dev(oracle.pack(B, a)), dev(oracle.pack(B, b)), dev(oracle.pack(B, c))
+        bs.bsfp_set_variant(f, "fma2", bs.VARIANT_STREAMED)
+        out = torch.full_like(pa, -1)
+        bs.bsfp_fma2(f, pa, pb, pc, out, n)
+        got = out.cpu().numpy().view(np.uint32).reshape(B, -1)
+        want = oracle.pack(B, oracle.fma2(E, M, rnd, a, b, c))
+        assert (got == want).all(), "fma2 1/%d/%d rnd=%d n=%d" % (E, M, rnd, n)
+    bs.bsfp_set_variant(f, "fma2", 0, 0)
+    assert bs.bsfp_fault_status() == 0
+
+
+@pytest.mark.parametrize("E,M", FMA2_STREAM_FORMATS)
+def test_streamed_fma2_several_rounds_of_the_ring(E, M):
+    """NST + 2 tiles per block and a ragged last tile: streamed and
+    grid-stride fma2 agree on every word of the output planes in all four
+    modes, and sampled elements plus the tail agree with the oracle."""
+    B = 1 + E + M
+    TW, NST = shape(E, M, "fma2")
+    n = bs.bsfp_num_sms() * (NST + 2) * 32 * TW - 3 * 32 * TW // 2 + 4321
+    cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[bs.bsfp_container_bytes(bs.Format(E, M))]
+    std = bs.empty_standard(bs.Format(E, M), n)
+    planes = []
+    for seed in (7101, 7102, 7103):
+        bs.bsfp_synth_fp_values(bs.Format(E, M), n, seed, 0, 0, std)
+        p = bs.empty_bitslice(bs.Format(E, M), n)
+        bs.bsfp_pack(bs.Format(E, M), std, n, p)
+        planes.append(p)
+    rng = np.random.default_rng(E * 64 + M + 1)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 4096), np.arange(n - 64, n)])).astype(np.int64)
+    xs = [synth.fp_values_at(E, M, idx, seed) for seed in (7101, 7102, 7103)]
+    idx_t = torch.from_numpy(idx).cuda()
+    ref = bs.empty_bitslice(bs.Format(E, M), n)
+    got = bs.empty_bitslice(bs.Format(E, M), n)
+    for rnd in MODES:
+        f = bs.Format(E, M, rnd)
+        bs.bsfp_set_variant(f, "fma2", bs.bsfp_variants_compiled(f, "fma2")[0])
+        bs.bsfp_fma2(f, planes[0], planes[1], planes[2], ref, n)
+        bs.bsfp_set_variant(f, "fma2", bs.VARIANT_STREAMED)
+        got.fill_(-1)
+        bs.bsfp_fma2(f, planes[0], planes[1], planes[2], got, n)
+        bs.bsfp_set_variant(f, "fma2", 0, 0)
+        assert torch.equal(got, ref), "fma2 1/%d/%d rnd=%d: streamed != grid-stride" % (E, M, rnd)
+        bs.bsfp_unpack(f, got, n, std)
+        res = std[idx_t].cpu().numpy().view(cdt).astype(np.uint32)
+        want = oracle.fma2(E, M, rnd, *xs)
+        bad = np.nonzero(res != want)[0]
+        assert not len(bad), "fma2 1/%d/%d rnd=%d: %d bad, first idx %d" % (E, M, rnd, len(bad), idx[bad[0]])
     assert bs.bsfp_fault_status() == 0
     del planes, ref, got, std
     torch.cuda.empty_cache()
@@ -209,7 +278,7 @@ def test_bounded_wait_runs_out_and_reports():
     with pytest.raises(bs.BsfpError):
         bs.bsfp_stream_selftest(f, "mul", a, b, out, n, tiles, 1 << 22)    # tile out of range
     with pytest.raises(bs.BsfpError):
-        bs.bsfp_stream_selftest(f, "fma2", a, b, out, n, 0, 1 << 22)       # no streamed fma2
+        bs.bsfp_stream_selftest(f, "fma2", a, b, out, n, 0, 1 << 22)       # add/sub and mul only
     bs.bsfp_stream_selftest(f, "mul", a, b, out, n, -1, 1 << 22)           # nothing withheld
     assert bs.bsfp_fault_status() == 0
     bs.bsfp_stream_selftest(f, "mul", a, b, out, n, tiles // 2, 1 << 22)
@@ -228,7 +297,7 @@ def test_bounded_wait_runs_out_and_reports():
     bs.bsfp_set_variant(f, "mul", 0, 0)
 
 
-@pytest.mark.parametrize("op", ["add", "mul"])
+@pytest.mark.parametrize("op", ["add", "mul", "div"])
 def test_in_place_output(op):
     """out may equal an input (the C ABI allows exact aliasing): the streamed
     kernel reads a tile into shared memory before any of its columns is
@@ -251,46 +320,63 @@ def test_in_place_output(op):
     bs.bsfp_set_variant(f, op, 0, 0)
 
 
-def _streamed_mul_formats():
+BANDS = {"mul": (12, 24, 1), "fma2": (10, 19, 4), "div": (8, 17, 3)}   # planes from, to; fewest fraction bits
+
+
+def _streamed_band_formats(op):
     fm = []
     for E in range(2, 9):
         for M in range(1, 24):
             if 1 + E + M <= 32 and (E, M) not in STREAM_FORMATS and \
-                    bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(E, M), "mul"):
+                    bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(E, M), op):
                 fm.append((E, M))
     return fm
 
 
-def test_streamed_mul_covers_the_band_of_12_to_24_planes():
-    fm = _streamed_mul_formats()
-    assert fm and all(12 <= 1 + E + M <= 24 for E, M in fm)
+@pytest.mark.parametrize("op", ["mul", "fma2", "div"])
+def test_streamed_band_covers_its_plane_counts(op):
+    """mul: the formats of 12..24 planes outside the tuned set; fma2: those
+    of 10..19 planes with 4 fraction bits or more; division: those of 8..17
+    planes with 3 fraction bits or more."""
+    lo, hi, mlo = BANDS[op]
+    fm = _streamed_band_formats(op)
+    assert fm and all(lo <= 1 + E + M <= hi and M >= mlo for E, M in fm)
     assert len(fm) == sum(1 for E in range(2, 9) for M in range(1, 24)
-                          if 12 <= 1 + E + M <= 24 and (E, M) not in STREAM_FORMATS + [(8, 23)])
+                          if lo <= 1 + E + M <= hi and M >= mlo and (E, M) not in STREAM_FORMATS + [(8, 23)])
 
 
+@pytest.mark.parametrize("op", ["mul", "fma2", "div"])
 @pytest.mark.parametrize("E", range(2, 9))
-def test_streamed_mul_of_every_format_in_the_band_vs_oracle(E):
-    """Formats of 12..24 planes outside the tuned set have a streamed mul (the
-    default up to 16 planes, the autotuner's choice beyond).  For each of
-    them, RN and RZ, forced streamed at every size: inside one tile, and three
-    tiles plus a ragged tail, every word of the output planes (padding
-    included) against the oracle."""
-    for (e, M) in _streamed_mul_formats():
+def test_streamed_band_of_every_format_vs_oracle(op, E):
+    """Formats outside the tuned set with a streamed mul (12..24 planes: the
+    default up to 16, the autotuner's choice beyond), fma2 (10..19 planes, 4
+    fraction bits or more, the default; the addend's planes in the ring up to
+    13 planes, loaded from global memory beyond) or division (8..17 planes, 3 fraction bits or more:
+    the default from 4).  For each of them, RN and RZ, forced
+    streamed at every size: inside one tile, and three tiles plus a ragged
+    tail, every word of the output planes (padding included) against the
+    oracle."""
+    for (e, M) in _streamed_band_formats(op):
         if e != E:
             continue
         B = 1 + E + M
-        TW, _ = shape(E, M, "mul")
+        TW, _ = shape(E, M, op)
         for n in (77, 3 * 32 * TW + 77):
             a = synth.fp_values(E, M, n, 900 + M).astype(np.uint32)
             b = synth.fp_values(E, M, n, 950 + M).astype(np.uint32)
-            pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+            c = synth.fp_values(E, M, n, 975 + M).astype(np.uint32)
+            pa, pb, pc = dev(oracle.pack(B, a)), dev(oracle.pack(B, b)), dev(oracle.pack(B, c))
             for rnd in (0, 1):
                 f = bs.Format(E, M, rnd)
-                bs.bsfp_set_variant(f, "mul", bs.VARIANT_STREAMED)
+                bs.bsfp_set_variant(f, op, bs.VARIANT_STREAMED)
                 out = torch.full_like(pa, -1)
-                bs.bsfp_mul(f, pa, pb, out, n)
-                bs.bsfp_set_variant(f, "mul", 0, 0)
+                if op == "fma2":
+                    bs.bsfp_fma2(f, pa, pb, pc, out, n)
+                else:
+                    bs.bsfp_op(op, f, pa, pb, out, n)
+                bs.bsfp_set_variant(f, op, 0, 0)
                 got = out.cpu().numpy().view(np.uint32).reshape(B, -1)
-                want = oracle.pack(B, oracle.binop("mul", E, M, rnd, a, b))
-                assert (got == want).all(), "mul 1/%d/%d rnd=%d n=%d" % (E, M, rnd, n)
+                want = oracle.pack(B, oracle.fma2(E, M, rnd, a, b, c) if op == "fma2" else
+                                   oracle.binop(op, E, M, rnd, a, b))
+                assert (got == want).all(), "%s 1/%d/%d rnd=%d n=%d" % (op, E, M, rnd, n)
     assert bs.bsfp_fault_status() == 0
