@@ -14,7 +14,7 @@
  *   div, 8 to 17 planes and at least 3 fraction bits: the default from 4
  *     fraction bits on, where over the sweep (2^26 elements) it was faster
  *     than the grid-stride kernel in all but two of the 82 format-modes
- *     (median 5%, up to 11%; the other two within 0.3%).  With 3 fraction
+ *     (median 4.5%, up to 11%; the other two within 0.3%).  With 3 fraction
  *     bits it won under RN and lost under RZ by up to 5%, so there the
  *     autotuner picks; with 2 it lost everywhere and is not compiled.
  *   fma2, 10 to 19 planes and at least 4 fraction bits: the default
