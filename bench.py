@@ -742,9 +742,14 @@ def run_sweep(bs, torch, args, rank, hbm, L):
     n = args.sweep_n
     stream = torch.cuda.current_stream()
     timer = DeviceTimer(torch, stream)
+    only = {tuple(int(x) for x in fm.split("/")) for fm in args.sweep_formats.split(",")} if args.sweep_formats \
+        else None
+    sweep_ops = tuple(op for op in SWEEP_OPS if op in args.sweep_ops.split(","))
     rows = []
     for E in range(3, 9):
         for M in range(2, 24):
+            if only is not None and (E, M) not in only:
+                continue
             B = 1 + E + M
             f0 = bs.Format(E, M, 0)
             std = bs.empty_standard(f0, n)
@@ -758,7 +763,7 @@ def run_sweep(bs, torch, args, rank, hbm, L):
             modes = (0, 1, 2, 3) if (E, M) in FTZ_FORMATS else (0, 1)
             for rnd in modes:
                 f = bs.Format(E, M, rnd)
-                for op in SWEEP_OPS:
+                for op in sweep_ops:
                     t = timer.ms(lambda: bs.bsfp_op(op, f, ops_[0], ops_[1], out, n, c=ops_[2], stream=stream),
                                  reps=3) * 1e-3
                     nin = 3 if op == "fma2" else 2
@@ -772,14 +777,16 @@ def run_sweep(bs, torch, args, rank, hbm, L):
                                  "frac": (n / t) / min(r_hbm, r_alu)})
             del ops_, out, std
     summary = {"formats": len({r["fmt"] for r in rows}), "elements": n}
+    if not rows:
+        return summary
     for rnd in ("RN", "RZ"):
-        for op in SWEEP_OPS:
+        for op in sweep_ops:
             sel = [r for r in rows if r["op"] == op and r["rnd"] == rnd]
             fr = np.array([r["frac"] for r in sel])
             summary["%s_%s" % (op, rnd)] = {"frac_min": float(fr.min()), "frac_median": float(np.median(fr)),
                                             "frac_max": float(fr.max()),
                                             "alu_bound_formats": sum(1 for r in sel if r["bound"] == "alu")}
-    for op in SWEEP_OPS:
+    for op in sweep_ops:
         rn = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN"}
         rz = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RZ"}
         tr = np.array([rz[k]["ms"] / rn[k]["ms"] for k in rn])
@@ -787,7 +794,7 @@ def run_sweep(bs, torch, args, rank, hbm, L):
         summary["rz_over_rn_%s" % op] = {"time_median": float(np.median(tr)), "time_min": float(tr.min()),
                                          "gates_median": float(np.median(gr)), "gates_min": float(gr.min())}
     # flush to zero against gradual underflow, on the formats compiled with it
-    for op in SWEEP_OPS:
+    for op in sweep_ops:
         pl = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN"}
         fz = {r["fmt"]: r for r in rows if r["op"] == op and r["rnd"] == "RN_FTZ"}
         summary["ftz_over_rn_%s" % op] = {k: {"time": fz[k]["ms"] / pl[k]["ms"],
@@ -930,6 +937,9 @@ def main(argv=None):
     ap.add_argument("--sweep-n", type=int, default=1 << 26,
                     help="elements per vector in the format sweep (0 skips it)")
     ap.add_argument("--sweep-out", default=None, help="write the full sweep table (JSON) here")
+    ap.add_argument("--sweep-formats", default="",
+                    help="comma-separated E/M (e.g. 4/7,6/7): sweep only these formats (default: all)")
+    ap.add_argument("--sweep-ops", default=",".join(SWEEP_OPS), help="comma-separated ops of the sweep")
     ap.add_argument("--section", default=None,
                     choices=["conversions", "small", "integers", "sweep", "batched", "serving", "e2e"],
                     help="run only this section of the bench and print it (no main timed loop)")

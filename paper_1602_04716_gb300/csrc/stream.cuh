@@ -204,8 +204,10 @@ __global__ void __launch_bounds__(StreamShape<E, M, OPC>::THREADS) stream_kernel
                 const uint32_t dst = smem_addr(ring + (size_t)s * NIN * TW);
 #pragma unroll 1
                 for (int q = 0; q < NIN; ++q) {
+                    /* NIN == 2B outside the fma2 ring: the addend test folds away */
                     const uint32_t* src = (q < B) ? p.a + (int64_t)q * p.S
-                                        : (q < 2 * B ? p.b + (int64_t)(q - B) * p.S : p.c + (int64_t)(q - 2 * B) * p.S);
+                                        : ((NIN == 2 * B || q < 2 * B) ? p.b + (int64_t)(q - B) * p.S
+                                                                       : p.c + (int64_t)(q - 2 * B) * p.S);
                     bulk_copy_g2s(dst + (uint32_t)(q * TW * 4), src + t * TW, bytes, bar);
                 }
             }
