@@ -211,6 +211,53 @@ def test_streamed_fma2_several_rounds_of_the_ring(E, M):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("E,M,op", [(4, 4, "add"), (4, 4, "mul"), (5, 7, "add"), (5, 7, "mul"), (5, 7, "div"),
+                                     (5, 7, "fma2"), (8, 7, "fma2"), (6, 9, "div")])
+def test_uneven_rounds_of_tiles(E, M, op):
+    """2.4 tiles per block: some blocks take three tiles and others two, and
+    the last tile is ragged.  For the adder, the multiplier, the divider and
+    fma2 (with the addend in the ring and from global memory): streamed
+    against grid-stride on every word of the output planes (RN and RZ), and
+    sampled elements against the oracle."""
+    B = 1 + E + M
+    TW, _ = shape(E, M, op)
+    n = int(2.4 * bs.bsfp_num_sms() * 32 * TW) + 333
+    f0 = bs.Format(E, M)
+    planes = []
+    std = bs.empty_standard(f0, n)
+    for seed in (7301, 7302, 7303):
+        bs.bsfp_synth_fp_values(f0, n, seed, 0, 0, std)
+        p = bs.empty_bitslice(f0, n)
+        bs.bsfp_pack(f0, std, n, p)
+        planes.append(p)
+    cdt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[bs.bsfp_container_bytes(f0)]
+    rng = np.random.default_rng(B * 7 + len(op))
+    idx = np.unique(np.concatenate([rng.integers(0, n, 2048), np.arange(n - 40, n)])).astype(np.int64)
+    xs = [synth.fp_values_at(E, M, idx, seed) for seed in (7301, 7302, 7303)]
+    idx_t = torch.from_numpy(idx).cuda()
+    ref = bs.empty_bitslice(f0, n)
+    got = bs.empty_bitslice(f0, n)
+    for rnd in (0, 1):
+        f = bs.Format(E, M, rnd)
+        c = planes[2] if op == "fma2" else None
+        bs.bsfp_set_variant(f, op, bs.bsfp_variants_compiled(f, op)[0])
+        bs.bsfp_op(op, f, planes[0], planes[1], ref, n, c=c)
+        bs.bsfp_set_variant(f, op, bs.VARIANT_STREAMED)
+        assert bs.bsfp_variant_for(f, op, n) == bs.VARIANT_STREAMED
+        got.fill_(-1)
+        bs.bsfp_op(op, f, planes[0], planes[1], got, n, c=c)
+        bs.bsfp_set_variant(f, op, 0, 0)
+        assert torch.equal(got, ref), "%s 1/%d/%d rnd=%d: streamed != grid-stride" % (op, E, M, rnd)
+        bs.bsfp_unpack(f, got, n, std)
+        res = std[idx_t].cpu().numpy().view(cdt).astype(np.uint32)
+        want = oracle.binop(op, E, M, rnd, xs[0], xs[1], xs[2])
+        bad = np.nonzero(res != want)[0]
+        assert not len(bad), "%s 1/%d/%d rnd=%d: %d bad, first idx %d" % (op, E, M, rnd, len(bad), idx[bad[0]])
+    assert bs.bsfp_fault_status() == 0
+    del planes, ref, got, std
+    torch.cuda.empty_cache()
+
+
 def test_streamed_writes_nothing_outside_its_output():
     """Guard words of 4 KiB on both sides of the output planes survive a
     streamed launch whose last tile is ragged."""
