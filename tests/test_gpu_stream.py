@@ -344,27 +344,29 @@ def test_bounded_wait_runs_out_and_reports():
     bs.bsfp_set_variant(f, "mul", 0, 0)
 
 
-@pytest.mark.parametrize("op", ["add", "mul", "div"])
-def test_in_place_output(op):
+@pytest.mark.parametrize("E,M,op,alias", [(5, 7, "add", 0), (5, 7, "mul", 0), (5, 7, "div", 0), (5, 7, "mul", 1),
+                                           (5, 7, "fma2", 0), (5, 7, "fma2", 2), (8, 7, "fma2", 0),
+                                           (8, 7, "fma2", 2)])
+def test_in_place_output(E, M, op, alias):
     """out may equal an input (the C ABI allows exact aliasing): the streamed
     kernel reads a tile into shared memory before any of its columns is
-    written, so out = a gives the same result as a separate output."""
-    E, M = 5, 7
+    written, and fma2 with the addend from global memory (16 planes) reads
+    each thread's addend columns before it stores them, so out = a, b or c
+    gives the same result as a separate output."""
     B = 1 + E + M
     f = bs.Format(E, M)
     TW, NST = shape(E, M, op)
     n = bs.bsfp_num_sms() * (NST + 1) * 32 * TW + 999
-    a = synth.fp_values(E, M, n, 61).astype(np.uint32)
-    b = synth.fp_values(E, M, n, 62).astype(np.uint32)
-    pa, pb = dev(oracle.pack(B, a)), dev(oracle.pack(B, b))
+    x = [synth.fp_values(E, M, n, seed).astype(np.uint32) for seed in (61, 62, 63)]
+    p = [dev(oracle.pack(B, v)) for v in x]
     bs.bsfp_set_variant(f, op, bs.VARIANT_STREAMED)
-    bs.bsfp_op(op, f, pa, pb, pa, n)
+    bs.bsfp_op(op, f, p[0], p[1], p[alias], n, c=p[2] if op == "fma2" else None)
     torch.cuda.synchronize()
+    bs.bsfp_set_variant(f, op, 0, 0)
     rng = np.random.default_rng(5)
     idx = np.unique(np.concatenate([rng.integers(0, n, 20000), np.arange(n - 100, n)]))
-    got = oracle.unpack(B, pa.cpu().numpy().view(np.uint32), n)[idx]
-    assert (got == oracle.binop(op, E, M, 0, a[idx], b[idx])).all()
-    bs.bsfp_set_variant(f, op, 0, 0)
+    got = oracle.unpack(B, p[alias].cpu().numpy().view(np.uint32), n)[idx]
+    assert (got == oracle.binop(op, E, M, 0, x[0][idx], x[1][idx], x[2][idx])).all()
 
 
 BANDS = {"mul": (12, 24, 1), "fma2": (10, 19, 4), "div": (8, 17, 3)}   # planes from, to; fewest fraction bits
