@@ -853,9 +853,11 @@ def host_link_rates(torch, pinned, reps=3):
 
 def run_e2e(bs, torch, n, rank, args):
     """Per step, for both formats: the two operand vectors in page-locked host
-    memory (standard form) through bsfp_pipeline_run -- chunked copy in, pack,
-    bs_add and bs_mul, unpack, copy out over rotating streams -- into two
-    result vectors in page-locked host memory."""
+    memory (standard form) through the host-to-host pipeline -- chunked copy
+    in, pack, bs_add and bs_mul, unpack, copy out over rotating streams --
+    into two result vectors in page-locked host memory.  Both formats are
+    submitted back to back (bsfp_pipeline_submit) and the step waits once for
+    all four results (bsfp_pipeline_wait)."""
     host_in, host_out = {}, {}
     for E, M in FORMATS:
         f = bs.Format(E, M, RND)
@@ -879,9 +881,10 @@ def run_e2e(bs, torch, n, rank, args):
         for E, M in FORMATS:
             f = bs.Format(E, M, RND)
             (ha, hb), outs = host_in[(E, M)], host_out[(E, M)]
-            pipe.run(f, OPS, ha, hb, outs, n)
+            pipe.submit(f, OPS, ha, hb, outs, n)
             h2d += 2 * ha.numel() * ha.element_size()
             d2h += sum(o.numel() * o.element_size() for o in outs)
+        pipe.wait()
 
     for _ in range(max(1, min(args.warmup, 2))):
         step()

@@ -311,6 +311,22 @@ bsfp_status bsfp_pipeline_create(int64_t chunk, int32_t depth, bsfp_pipeline* ou
  * CUDA failures BSFP_ERR_CUDA. */
 bsfp_status bsfp_pipeline_run(bsfp_pipeline p, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,
                               const void* b, const void* c, void* const* outs, int64_t n);
+/* bsfp_pipeline_run without the final wait: the same checks (argument
+ * errors return before anything is enqueued), then every chunk's copies and
+ * kernels are enqueued and the call returns.  The chunks continue the
+ * rotation over the streams where the previous submission stopped, so
+ * several vectors (of any formats) submitted back to back keep both copy
+ * directions busy across the boundary instead of draining the pipeline
+ * between them.  The host arrays must stay valid and untouched until
+ * bsfp_pipeline_wait returns.  A submission that needs larger device
+ * buffers than the pipeline holds first waits for the work in flight. */
+bsfp_status bsfp_pipeline_submit(bsfp_pipeline p, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,
+                                 const void* b, const void* c, void* const* outs, int64_t n);
+/* Blocks until every result of the submissions so far is in host memory.
+ * Returns the first failure among those submissions that had started
+ * enqueueing work (BSFP_ERR_CUDA for a failed copy or launch), else BSFP_OK,
+ * and clears it; BSFP_ERR_NULL for a NULL pipeline. */
+bsfp_status bsfp_pipeline_wait(bsfp_pipeline p);
 void bsfp_pipeline_free(bsfp_pipeline p);
 
 /* -------------------------------------------------------------- serving --- */

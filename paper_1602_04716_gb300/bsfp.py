@@ -148,6 +148,8 @@ def _lib():
                 "bsfp_batch_run_noalloc": (i32, [ctypes.POINTER(bsfp_job), i32, p]),
                 "bsfp_pipeline_create": (i32, [i64, i32, ctypes.POINTER(p)]),
                 "bsfp_pipeline_run": (i32, [p, F, i32, ctypes.POINTER(i32), p, p, p, ctypes.POINTER(p), i64]),
+                "bsfp_pipeline_submit": (i32, [p, F, i32, ctypes.POINTER(i32), p, p, p, ctypes.POINTER(p), i64]),
+                "bsfp_pipeline_wait": (i32, [p]),
                 "bsfp_pipeline_free": (None, [p]),
                 "bsfp_server_create": (i32, [ctypes.POINTER(bsfp_server_options), ctypes.POINTER(p)]),
                 "bsfp_server_submit": (i32, [p, ctypes.POINTER(bsfp_job), ctypes.POINTER(i64)]),
@@ -462,12 +464,24 @@ class Pipeline:
         self._h = ctypes.c_void_p()
         _check(_lib().bsfp_pipeline_create(chunk, depth, ctypes.byref(self._h)), "bsfp_pipeline_create")
 
-    def run(self, f, ops, a, b, outs, n: int, c=None):
+    def _call(self, fn, f, ops, a, b, outs, n, c):
         ops = [OPS.get(o, o) for o in ops]
         arr = (ctypes.c_int32 * len(ops))(*ops)
         optr = (ctypes.c_void_p * len(outs))(*[_host_ptr(o) for o in outs])
-        _check(_lib().bsfp_pipeline_run(self._h, _fmt(f), len(ops), arr, _host_ptr(a), _host_ptr(b),
-                                        _host_ptr(c), optr, n), "bsfp_pipeline_run")
+        _check(getattr(_lib(), fn)(self._h, _fmt(f), len(ops), arr, _host_ptr(a), _host_ptr(b), _host_ptr(c),
+                                   optr, n), fn)
+
+    def run(self, f, ops, a, b, outs, n: int, c=None):
+        """outs[q] = ops[q](a, b [, c]) on host arrays; returns when done."""
+        self._call("bsfp_pipeline_run", f, ops, a, b, outs, n, c)
+
+    def submit(self, f, ops, a, b, outs, n: int, c=None):
+        """As run, but returns once the work is enqueued: the arrays must stay
+        untouched until wait() returns."""
+        self._call("bsfp_pipeline_submit", f, ops, a, b, outs, n, c)
+
+    def wait(self):
+        _check(_lib().bsfp_pipeline_wait(self._h), "bsfp_pipeline_wait")
 
     def close(self):
         if self._h:

@@ -45,6 +45,8 @@ struct bsfp_pipeline_st {
     int64_t chunk = 0;
     int depth = 0;
     int device = 0;
+    int64_t next = 0;         /* slot of the next chunk: the rotation goes on across submissions */
+    bsfp_status pending = BSFP_OK;   /* first failure of the submissions since the last wait */
     int64_t cap_std = 0;      /* bytes of each standard buffer */
     int64_t cap_bs = 0;       /* bytes of each bitslice buffer */
     int cap_ops = 0;
@@ -141,9 +143,9 @@ bsfp_status bsfp_pipeline_create(int64_t chunk, int32_t depth, bsfp_pipeline* ou
     return BSFP_OK;
 }
 
-bsfp_status bsfp_pipeline_run(bsfp_pipeline P, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,
-                              const void* b, const void* c, void* const* outs, int64_t n) {
-    NvtxRange range("bsfp_pipeline_run");
+bsfp_status bsfp_pipeline_submit(bsfp_pipeline P, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,
+                                 const void* b, const void* c, void* const* outs, int64_t n) {
+    NvtxRange range("bsfp_pipeline_submit");
     if (!P || !ops || !outs) return BSFP_ERR_NULL;
     if (!format_ok(f)) return BSFP_ERR_FORMAT;
     if (nops < 1 || nops > BSFP_PIPE_MAX_OPS || n < 0 || n > BSFP_MAX_N) return BSFP_ERR_SIZE;
@@ -165,9 +167,9 @@ bsfp_status bsfp_pipeline_run(bsfp_pipeline P, bsfp_format f, int32_t nops, cons
     const unsigned char* in[3] = {static_cast<const unsigned char*>(a), static_cast<const unsigned char*>(b),
                                   static_cast<const unsigned char*>(c)};
     bsfp_status st = BSFP_OK;
-    int64_t k = 0;
-    for (int64_t e0 = 0; e0 < n && st == BSFP_OK; e0 += chunk, ++k) {
-        PipeSlot& s = P->slots[(size_t)(k % P->depth)];
+    for (int64_t e0 = 0; e0 < n && st == BSFP_OK; e0 += chunk) {
+        PipeSlot& s = P->slots[(size_t)(P->next % P->depth)];
+        P->next = (P->next + 1) % P->depth;
         const int64_t m = (n - e0) < chunk ? (n - e0) : chunk;
         const bsfp_stream_t ss = reinterpret_cast<bsfp_stream_t>(s.stream);
         for (int i = 0; i < nin && st == BSFP_OK; ++i) {
@@ -185,12 +187,29 @@ bsfp_status bsfp_pipeline_run(bsfp_pipeline P, bsfp_format f, int32_t nops, cons
             }
         }
     }
-    /* the call returns when every result chunk is in host memory */
+    if (st != BSFP_OK && P->pending == BSFP_OK) P->pending = st;
+    return st;
+}
+
+bsfp_status bsfp_pipeline_wait(bsfp_pipeline P) {
+    if (!P) return BSFP_ERR_NULL;
+    bsfp_status st = P->pending;
+    P->pending = BSFP_OK;
     for (PipeSlot& s : P->slots) {
-        e = cudaStreamSynchronize(s.stream);
+        const cudaError_t e = cudaStreamSynchronize(s.stream);
         if (e != cudaSuccess && st == BSFP_OK) st = set_cuda_error(e);
     }
     return st;
+}
+
+bsfp_status bsfp_pipeline_run(bsfp_pipeline P, bsfp_format f, int32_t nops, const int32_t* ops, const void* a,
+                              const void* b, const void* c, void* const* outs, int64_t n) {
+    NvtxRange range("bsfp_pipeline_run");
+    if (!P) return BSFP_ERR_NULL;
+    /* the call returns when every result chunk is in host memory */
+    const bsfp_status st = bsfp_pipeline_submit(P, f, nops, ops, a, b, c, outs, n);
+    const bsfp_status w = bsfp_pipeline_wait(P);
+    return st != BSFP_OK ? st : w;
 }
 
 void bsfp_pipeline_free(bsfp_pipeline P) {

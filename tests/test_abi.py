@@ -219,6 +219,8 @@ def test_pipeline_arguments_validated_before_any_cuda_call():
     ops = (ctypes.c_int32 * 1)(0)
     outs = (ctypes.c_void_p * 1)(256)
     assert L.bsfp_pipeline_run(None, bs.Format(4, 3), 1, ops, 256, 256, None, outs, 10) == bs.ERR_NULL
+    assert L.bsfp_pipeline_submit(None, bs.Format(4, 3), 1, ops, 256, 256, None, outs, 10) == bs.ERR_NULL
+    assert L.bsfp_pipeline_wait(None) == bs.ERR_NULL
     L.bsfp_pipeline_free(None)
 
 

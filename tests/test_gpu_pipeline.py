@@ -65,6 +65,38 @@ def test_pipeline_default_chunks_and_growth():
     pipe.close()
 
 
+def test_pipeline_submissions_back_to_back():
+    """Several vectors of different formats, op lists and lengths submitted
+    back to back and waited for once: the chunks keep rotating over the
+    streams across the submissions (chunk counts not multiples of the
+    depth, a buffer growth in the middle), and every result equals the
+    oracle.  Then a failing submission is reported by its own return and a
+    later wait is clean."""
+    pipe = bs.Pipeline(chunk=4096, depth=3)
+    cases = [((4, 4), 4096 * 5 + 17, ["add", "mul"]), ((5, 7), 4096 * 4 + 1, ["mul", "sub", "fma2"]),
+             ((8, 23), 4096 * 2 + 300, ["div"]), ((4, 3), 999, ["add"]), ((5, 10), 4096 * 7, ["fma2", "add"])]
+    keep = []
+    for (E, M), n, ops in cases:
+        f = bs.Format(E, M, n % 2)
+        a, b, c = (_host(E, M, n, 31 * n + s, True) for s in (1, 2, 3))
+        outs = [_host(E, M, n, 0, True) for _ in ops]
+        pipe.submit(f, ops, a, b, outs, n, c=c)
+        keep.append((E, M, n % 2, n, ops, a, b, c, outs))
+    pipe.wait()
+    for E, M, rnd, n, ops, a, b, c, outs in keep:
+        dt = synth.container_dtype(1 + E + M)
+        av, bv, cv = (_np(x, dt).astype(np.uint32) for x in (a, b, c))
+        for op, o in zip(ops, outs):
+            want = oracle.binop(op, E, M, rnd, av, bv, cv)
+            assert (_np(o, dt).astype(np.uint32) == want).all(), "%s 1/%d/%d n=%d" % (op, E, M, n)
+    x = np.zeros(10, np.uint8)
+    with pytest.raises(bs.BsfpError) as ei:
+        pipe.submit(bs.Format(4, 3), ["fma2"], x, x, [x.copy()], 10)   # no addend
+    assert ei.value.status == bs.ERR_NULL
+    pipe.wait()
+    pipe.close()
+
+
 def test_pipeline_validation():
     pipe = bs.Pipeline(chunk=1024, depth=2)
     f = bs.Format(4, 3)
