@@ -905,6 +905,7 @@ def run_e2e(bs, torch, n, rank, args):
     link["overlapped_copy_ms_per_step"] = 1e3 * (h2d + d2h) / (link["both_directions_gbs"] * 1e9)
     return {"value": len(FORMATS) * len(OPS) * n / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k, "step_ms": per_step,
+            "median_step_ms": float(np.median(per_step)),
             "host_link": link,
             "path": "pinned host -> bsfp_pipeline_run (chunks of %d over %d streams: H2D, bsfp_pack, "
                     "bsfp_add + bsfp_mul, bsfp_unpack, D2H) -> pinned host, per format"
@@ -920,7 +921,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["bsfp", "reference"], default="bsfp")
     ap.add_argument("--n", type=int, default=N, help="elements per vector (default 2^28)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20,
+                    help="timed end-to-end steps (about 14 ms each); the value is their mean, so one slow step "
+                         "on a busy host weighs 1/steps")
     ap.add_argument("--e2e-chunk", type=int, default=0, help="pipeline chunk (elements; 0 = library default)")
     ap.add_argument("--e2e-depth", type=int, default=0, help="pipeline streams (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
