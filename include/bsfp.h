@@ -267,8 +267,10 @@ bsfp_status bsfp_launch_jobs(const bsfp_job* jobs, int32_t njobs, bsfp_stream_t 
  * counters.  Calls on one stream run one after another; calls that overlap
  * on the GPU (other streams, other host threads) race on the array and give
  * wrong results.  The first call on a device also looks up the array's device
- * address and the kernels' occupancy; make that first call before any stream
- * capture.
+ * address and the kernels' occupancy.  The call is meant to be issued
+ * directly on s, not captured into a CUDA graph: a captured call would copy
+ * `jobs` again from the caller's host array at every replay (for repeated
+ * batches in a graph, use a plan, bsfp_batch_plan_create).
  *
  * jobs is host memory read by an asynchronous copy on s: pageable memory is
  * staged before the call returns; page-locked memory must stay unchanged
