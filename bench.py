@@ -907,8 +907,8 @@ def run_e2e(bs, torch, n, rank, args):
             "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": k, "step_ms": per_step,
             "median_step_ms": float(np.median(per_step)),
             "host_link": link,
-            "path": "pinned host -> bsfp_pipeline_run (chunks of %d over %d streams: H2D, bsfp_pack, "
-                    "bsfp_add + bsfp_mul, bsfp_unpack, D2H) -> pinned host, per format"
+            "path": "pinned host -> bsfp_pipeline_submit per format, one bsfp_pipeline_wait per step (chunks "
+                    "of %d over %d streams: H2D, bsfp_pack, bsfp_add + bsfp_mul, bsfp_unpack, D2H) -> pinned host"
                     % (args.e2e_chunk or (1 << 23), args.e2e_depth or 4)}
 
 
