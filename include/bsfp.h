@@ -456,9 +456,15 @@ int64_t bsfp_gate_count(bsfp_format f, int32_t op);
  * planes into a shared-memory ring with TMA bulk copies (cp.async.bulk,
  * completed on mbarriers) while consumer warps run the circuit from it.  It
  * is compiled for add/sub and mul of 1/4/3, 1/4/4, 1/5/7, 1/5/10 and 1/8/7
- * in every rounding mode.  Results are identical in every variant; only the
- * speed differs.  (Not a construct of the paper, whose kernels are CPU
- * loops; Sec. 4 leaves the memory schedule to the implementation.) */
+ * in every rounding mode (and fma2 and division of those of them that lie in
+ * the bands below); and for every other format under RN and RZ: mul of 12 to
+ * 24 planes, fma2 of 10 to 19 planes with at least 4 fraction bits, and
+ * division of 8 to 17 planes with at least 3 fraction bits, where it is the
+ * default variant (the autotuner's choice instead for mul above 16 planes
+ * and division with 3 fraction bits).  bsfp_variants_compiled tells which.
+ * Results are identical in every variant; only the speed differs.  (Not a
+ * construct of the paper, whose kernels are CPU loops; Sec. 4 leaves the
+ * memory schedule to the implementation.) */
 #define BSFP_VARIANT_STREAMED 8
 /* Variant the op kernel will use for (format, op): 1, 2, 4 or
  * BSFP_VARIANT_STREAMED; -1 on a bad argument, 0 if the format is not
@@ -497,9 +503,9 @@ bsfp_status bsfp_stream_shape(bsfp_format f, int32_t op, int32_t* tile_words, in
  * the withheld tile run out, the block stops after letting its other copies
  * land, and the fault word (bsfp_fault_status) becomes 1; the output of the
  * blocks that stopped is incomplete, the device stays usable.  For tests of
- * the failure path; no counterpart in the paper.  BSFP_ERR_UNSUPPORTED if
- * (format, op) has no streamed kernel; BSFP_ERR_SIZE for an out-of-range
- * tile or bound. */
+ * the failure path; no counterpart in the paper.  Covers add, sub and mul:
+ * BSFP_ERR_UNSUPPORTED for another op or if (format, op) has no streamed
+ * kernel; BSFP_ERR_SIZE for an out-of-range tile or bound. */
 bsfp_status bsfp_stream_selftest(bsfp_format f, int32_t op, const uint32_t* a, const uint32_t* b, uint32_t* out,
                                  int64_t n, int64_t withhold_tile, int64_t wait_cycles, bsfp_stream_t s);
 /* Minimum tiles per SM for the streamed variant (default 2; 0 = always take
