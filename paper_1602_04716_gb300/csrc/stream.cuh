@@ -78,12 +78,17 @@ struct StreamShape {
      * for mul (more warps feed its logic pipe); 12 x 2 for B = 16, except
      * mul 1/8/7 at 14 x 2 (1/5/10 mul gained nothing and its job-list form
      * spills there, and the adders stream at the copy bandwidth with 12).
-     * Wider formats: 8 x 2 up to 24 planes, 6 x 2 beyond, so that the ring
-     * of 2B planes fits and each thread may hold the wide multipliers'
-     * registers. */
+     * Wider formats: 11 x 2 up to 20 planes, 8 x 2 up to 24, 6 x 2 beyond,
+     * so that the ring of 2B planes fits and each thread may hold the wide
+     * multipliers' registers (up to 168).  The consumer warps are spread over
+     * the four schedulers by warp index mod 4, so a logic-bound kernel wants
+     * a count that loads them evenly: 8 (2 each) and 11 (3, 3, 3 and 2 beside
+     * the producer) ran 7-13% faster than 9 and 10 on six multipliers of
+     * 17-20 planes, and 11 x 2 beat 8 x 2 by 4-8% there. */
     static constexpr int NC_ADDMUL = B <= 9 ? 11
                             : (B <= 13 ? (OPC == OPC_ADDSUB ? 11 : 15)
-                                       : (B <= 16 ? ((OPC == OPC_MUL && E == 8) ? 14 : 12) : (B <= 24 ? 8 : 6)));
+                                       : (B <= 16 ? ((OPC == OPC_MUL && E == 8) ? 14 : 12)
+                                                  : (B <= 20 ? 11 : (B <= 24 ? 8 : 6))));
     /* division (8 to 17 planes): 15 x 2 up to 13 planes, 12 x 2 beyond,
      * each faster than 11 x 3, 8 x 3 and the one-word-per-thread shapes on
      * 2^27-element operands.  fma2 (10 to 19 planes): 11 x 2 with the

@@ -4,13 +4,14 @@
  * class's band, compiled once per exponent width and op class with
  * -DBSFP_SE=E -DBSFP_SOPC=<1 mul, 2 fma2, 3 div>.
  *
- *   mul, 12 to 24 planes: for formats of at most 16 planes it becomes the
+ *   mul, 12 to 24 planes: for formats of at most 20 planes it becomes the
  *     variant a mul call takes by default (BinopEntry::preferred): measured
  *     over the sweep it beat the grid-stride kernel in nearly every one of
- *     them.  For 17 to 24 planes it won for some formats and lost for others
- *     (its 8 consumer warps have the registers of the wide multipliers but
- *     hide less latency), so there the grid-stride kernel stays the default
- *     and the autotuner picks per format and mode.
+ *     those up to 16 planes, and with 11 consumer warps it was 4-10% faster
+ *     on six multipliers of 17-20 planes.  For 21 to 24 planes (8 consumer
+ *     warps, all the ring holds) it won for some formats and lost for
+ *     others, so there the grid-stride kernel stays the default and the
+ *     autotuner picks per format and mode.
  *   div, 8 to 17 planes and at least 3 fraction bits: the default from 4
  *     fraction bits on, where over the sweep (2^26 elements) it was faster
  *     than the grid-stride kernel in all but two of the 82 format-modes
@@ -43,7 +44,7 @@ static void add_stream_band(BinopEntry& e) {
     e.stream_tw = StreamShape<E, M, OPC>::TW;
     e.stream_nst = StreamShape<E, M, OPC>::NST;
     e.wpt_mask |= (unsigned)VARIANT_STREAMED;
-    if constexpr (OPC == OPC_DIV ? M >= 4 : (OPC == OPC_FMA2 || 1 + E + M <= 16)) e.preferred = VARIANT_STREAMED;
+    if constexpr (OPC == OPC_DIV ? M >= 4 : (OPC == OPC_FMA2 || 1 + E + M <= 20)) e.preferred = VARIANT_STREAMED;
 }
 
 template <int E, int M, int OPC>

@@ -398,7 +398,7 @@ def test_streamed_band_covers_its_plane_counts(op):
 @pytest.mark.parametrize("E", range(2, 9))
 def test_streamed_band_of_every_format_vs_oracle(op, E):
     """Formats outside the tuned set with a streamed mul (12..24 planes: the
-    default up to 16, the autotuner's choice beyond), fma2 (10..19 planes, 4
+    default up to 20, the autotuner's choice beyond), fma2 (10..19 planes, 4
     fraction bits or more, the default; the addend's planes in the ring up to
     13 planes, loaded from global memory beyond) or division (8..17 planes, 3 fraction bits or more:
     the default from 4).  For each of them, RN and RZ, forced
