@@ -459,8 +459,8 @@ int64_t bsfp_gate_count(bsfp_format f, int32_t op);
  * in every rounding mode (and fma2 and division of those of them that lie in
  * the bands below); and for every other format under RN and RZ: mul of 12 to
  * 24 planes, fma2 of 10 to 19 planes with at least 4 fraction bits, and
- * division of 8 to 17 planes with at least 3 fraction bits, where it is the
- * default variant (the autotuner's choice instead for mul above 16 planes
+ * division of 8 to 24 planes with at least 3 fraction bits, where it is the
+ * default variant (the autotuner's choice instead for mul above 20 planes
  * and division with 3 fraction bits).  bsfp_variants_compiled tells which.
  * Results are identical in every variant; only the speed differs.  (Not a
  * construct of the paper, whose kernels are CPU loops; Sec. 4 leaves the

@@ -44,7 +44,7 @@ void register_int_w1(); void register_int_w17();
 /* streamed kernels, one translation unit per format (stream_inst.cu) */
 void register_stream_e4_m3(); void register_stream_e4_m4(); void register_stream_e5_m7();
 void register_stream_e5_m10(); void register_stream_e8_m7();
-/* streamed mul (12..24 planes), fma2 (10..17) and division (8..17) of the
+/* streamed mul (12..24 planes), fma2 (10..19) and division (8..24) of the
  * other formats, one unit per exponent width and op class
  * (stream_band_inst.cu) */
 void register_stream_mul_e2(); void register_stream_mul_e3(); void register_stream_mul_e4();

@@ -49,9 +49,9 @@ namespace bsfp {
  *   every other format, RN and RZ (stream_band_inst.cu): mul of 12 to 24
  *     planes -- the band where the multiplier sits near the crossover of
  *     logic and HBM bounds and the grid-stride kernel, with few warps
- *     resident, leaves both pipes idle part of the time; division of 8 to 17
+ *     resident, leaves both pipes idle part of the time; division of 8 to 24
  *     planes with at least 3 fraction bits, where the same holds: the divider
- *     needs 64-128 registers a thread in the grid-stride kernel (4-8 warps
+ *     needs 64-168 registers a thread in the grid-stride kernel (3-8 warps
  *     per scheduler), while with 2 fraction bits it is light and HBM-bound
  *     and the grid-stride kernel was faster; fma2 of 10 to 19 planes with
  *     at least 4 fraction bits, bound by the logic pipe from about 11 planes
@@ -59,7 +59,7 @@ namespace bsfp {
  *     multiplier runs (with fewer fraction bits the multiplier is light, the
  *     op HBM-bound, and the grid-stride kernel was faster). */
 constexpr bool stream_format(int E, int M) { return tuned_format(E, M) && 1 + E + M <= 16; }
-constexpr bool stream_div_format(int E, int M) { return 1 + E + M >= 8 && 1 + E + M <= 17 && M >= 3; }
+constexpr bool stream_div_format(int E, int M) { return 1 + E + M >= 8 && 1 + E + M <= 24 && M >= 3; }
 constexpr bool stream_fma2_format(int E, int M) { return 1 + E + M >= 10 && 1 + E + M <= 19 && M >= 4; }
 constexpr bool stream_band_format(int E, int M, int opc) {
     return opc == OPC_MUL    ? (1 + E + M >= 12 && 1 + E + M <= 24)
@@ -89,9 +89,11 @@ struct StreamShape {
                             : (B <= 13 ? (OPC == OPC_ADDSUB ? 11 : 15)
                                        : (B <= 16 ? ((OPC == OPC_MUL && E == 8) ? 14 : 12)
                                                   : (B <= 20 ? 11 : (B <= 24 ? 8 : 6))));
-    /* division (8 to 17 planes): 15 x 2 up to 13 planes, 12 x 2 beyond,
+    /* division (8 to 24 planes): 15 x 2 up to 13 planes, 12 x 2 up to 17,
      * each faster than 11 x 3, 8 x 3 and the one-word-per-thread shapes on
-     * 2^27-element operands.  fma2 (10 to 19 planes): 11 x 2 with the
+     * 2^27-element operands; then, as for mul, 11 x 2 up to 20 planes and
+     * 8 x 2 up to 24 (1-6% faster than the grid-stride kernel on seven
+     * dividers of 18-22 planes at 2^26 elements).  fma2 (10 to 19 planes): 11 x 2 with the
      * addend's planes in the ring up to 13 planes; 12 x 2 beyond, where the
      * ring holds only a and b and the consumers load the addend from global
      * memory once the product is done (3B planes of 12 warps' tiles would
@@ -100,7 +102,8 @@ struct StreamShape {
      * thread, and 10 x 2, were slower.  18 and 19 planes take 11 x 2 with
      * the addend from global memory, so that 2B planes still fit. */
     static constexpr int NC_FMA2 = B <= 13 ? 11 : (B <= 17 ? 12 : 11);
-    static constexpr int NC = OPC == OPC_DIV ? (B <= 13 ? 15 : 12) : (OPC == OPC_FMA2 ? NC_FMA2 : NC_ADDMUL);
+    static constexpr int NC_DIV = B <= 13 ? 15 : (B <= 17 ? 12 : (B <= 20 ? 11 : 8));
+    static constexpr int NC = OPC == OPC_DIV ? NC_DIV : (OPC == OPC_FMA2 ? NC_FMA2 : NC_ADDMUL);
     static constexpr int NST = (OPC == OPC_DIV || OPC == OPC_FMA2) ? 2
                              : (B <= 9 ? 4 : ((B <= 13 && OPC == OPC_ADDSUB) ? 3 : 2));   /* ring stages */
     static constexpr bool Z_IN_RING = OPC == OPC_FMA2 && B <= 13;   /* fma2: the addend's planes in the ring */

@@ -12,10 +12,11 @@
  *     warps, all the ring holds) it won for some formats and lost for
  *     others, so there the grid-stride kernel stays the default and the
  *     autotuner picks per format and mode.
- *   div, 8 to 17 planes and at least 3 fraction bits: the default from 4
+ *   div, 8 to 24 planes and at least 3 fraction bits: the default from 4
  *     fraction bits on, where over the sweep (2^26 elements) it was faster
- *     than the grid-stride kernel in all but two of the 82 format-modes
- *     (median 4.5%, up to 11%; the other two within 0.3%).  With 3 fraction
+ *     than the grid-stride kernel in all but two of the 82 format-modes of
+ *     8-17 planes (median 4.5%, up to 11%; the other two within 0.3%), and
+ *     on seven dividers of 18-22 planes by 1-6%.  With 3 fraction
  *     bits it won under RN and lost under RZ by up to 5%, so there the
  *     autotuner picks; with 2 it lost everywhere and is not compiled.
  *   fma2, 10 to 19 planes and at least 4 fraction bits: the default

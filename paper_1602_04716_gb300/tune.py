@@ -168,7 +168,7 @@ def main(argv=None):
                                                                         op, best[0], best[1], table[best]), flush=True)
             del a, b, c, o
             torch.cuda.empty_cache()
-    # mul (12..24 planes), fma2 (10..17) and division (8..17) of the other formats that have a
+    # mul (12..24 planes), fma2 (10..19) and division (8..24) of the other formats that have a
     # streamed kernel: the grid-stride default against the streamed kernel, per format and rounding,
     # at the sweep's size
     for E in range(2, 9):

@@ -127,13 +127,14 @@ def test_variants_and_overrides():
     assert bs.bsfp_variant(g, "mul") == bs.VARIANT_STREAMED
     assert len(bs.bsfp_variants_compiled(g, "add")) == 1
     assert bs.bsfp_variants_compiled(bs.Format(3, 5), "mul") == [2]   # 9 planes: below the streamed band
-    # division: streamed for 8..17 planes and 3 fraction bits or more, the default for the formats
+    # division: streamed for 8..24 planes and 3 fraction bits or more, the default for the formats
     # outside the tuned set from 4 fraction bits on
     assert bs.bsfp_variants_compiled(f, "div") == [1, 2, 4, bs.VARIANT_STREAMED]
     assert bs.bsfp_variants_compiled(g, "div") == [2, bs.VARIANT_STREAMED]
     assert bs.bsfp_variant(g, "div") == bs.VARIANT_STREAMED
     assert bs.bsfp_variants_compiled(bs.Format(3, 5), "div") == [2, bs.VARIANT_STREAMED]
-    assert bs.bsfp_variants_compiled(bs.Format(7, 10), "div") == [2]   # 18 planes: above the band
+    assert bs.bsfp_variants_compiled(bs.Format(7, 10), "div") == [2, bs.VARIANT_STREAMED]   # 18 planes
+    assert bs.bsfp_variants_compiled(bs.Format(8, 16), "div") == [1]   # 25 planes: above the band
     assert bs.bsfp_variants_compiled(bs.Format(3, 2), "div") == [2]    # 6 planes: below it
     assert bs.bsfp_variants_compiled(bs.Format(6, 2), "div") == [2]    # 2 fraction bits: HBM-bound, none
     # fma2: streamed for 10..19 planes and 4 fraction bits or more, the default for the formats outside
@@ -330,6 +331,8 @@ def test_stream_shape_query():
     assert bs.bsfp_stream_shape(bs.Format(5, 7), "div") == (32 * 15 * 2, 2)
     assert bs.bsfp_stream_shape(bs.Format(3, 5, bs.RZ), "div") == (32 * 15 * 2, 2)
     assert bs.bsfp_stream_shape(bs.Format(7, 9), "div") == (32 * 12 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(8, 10, bs.RZ), "div") == (32 * 11 * 2, 2)
+    assert bs.bsfp_stream_shape(bs.Format(8, 13), "div") == (32 * 8 * 2, 2)
     assert bs.bsfp_stream_shape(bs.Format(5, 7), "fma2") == (32 * 11 * 2, 2)
     assert bs.bsfp_stream_shape(bs.Format(8, 7, bs.RZ_FTZ), "fma2") == (32 * 12 * 2, 2)
     assert bs.bsfp_stream_shape(bs.Format(6, 9), "fma2") == (32 * 12 * 2, 2)

@@ -65,7 +65,7 @@ def test_streamed_variant_is_compiled_where_documented():
         for op in ("mul", "fma2", "div"):
             assert bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(bs.Format(E, M), op)
     # outside the tuned set (RN, RZ): the streamed mul for 12..24 planes, fma2 for 10..19 and division
-    # for 8..17, no streamed add
+    # for 8..24, no streamed add
     assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(6, 9, 1), "mul")
     assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(6, 9, 1), "fma2")
     assert bs.VARIANT_STREAMED in bs.bsfp_variants_compiled(bs.Format(6, 9, 1), "div")
@@ -369,7 +369,7 @@ def test_in_place_output(E, M, op, alias):
     assert (got == oracle.binop(op, E, M, 0, x[0][idx], x[1][idx], x[2][idx])).all()
 
 
-BANDS = {"mul": (12, 24, 1), "fma2": (10, 19, 4), "div": (8, 17, 3)}   # planes from, to; fewest fraction bits
+BANDS = {"mul": (12, 24, 1), "fma2": (10, 19, 4), "div": (8, 24, 3)}   # planes from, to; fewest fraction bits
 
 
 def _streamed_band_formats(op):
@@ -385,7 +385,7 @@ def _streamed_band_formats(op):
 @pytest.mark.parametrize("op", ["mul", "fma2", "div"])
 def test_streamed_band_covers_its_plane_counts(op):
     """mul: the formats of 12..24 planes outside the tuned set; fma2: those
-    of 10..19 planes with 4 fraction bits or more; division: those of 8..17
+    of 10..19 planes with 4 fraction bits or more; division: those of 8..24
     planes with 3 fraction bits or more."""
     lo, hi, mlo = BANDS[op]
     fm = _streamed_band_formats(op)
@@ -400,7 +400,7 @@ def test_streamed_band_of_every_format_vs_oracle(op, E):
     """Formats outside the tuned set with a streamed mul (12..24 planes: the
     default up to 20, the autotuner's choice beyond), fma2 (10..19 planes, 4
     fraction bits or more, the default; the addend's planes in the ring up to
-    13 planes, loaded from global memory beyond) or division (8..17 planes, 3 fraction bits or more:
+    13 planes, loaded from global memory beyond) or division (8..24 planes, 3 fraction bits or more:
     the default from 4).  For each of them, RN and RZ, forced
     streamed at every size: inside one tile, and three tiles plus a ragged
     tail, every word of the output planes (padding included) against the
