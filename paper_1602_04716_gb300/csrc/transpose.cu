@@ -14,9 +14,12 @@
  *  pack:   coalesced 16-byte loads of the tile -> shared memory -> each lane
  *          reads its column (32 elements), transposes it in registers and
  *          stores its B plane words; the warp's stores are 128-byte rows.
+ *          The next tile's loads are issued before the current one is
+ *          staged.
  *  unpack: each lane loads its column's B plane words (128-byte rows per
  *          warp), transposes them into 32 elements, writes them to shared
- *          memory -> coalesced 16-byte stores of the tile.
+ *          memory -> coalesced 16-byte stores of the tile.  The next tile's
+ *          plane words are loaded before the current one is transposed.
  *
  * There is no cross-lane shuffle: a column's transpose is 64 (CB = 1), 128
  * (CB = 2) or 256 (CB = 4) logic instructions of one thread.  Tiles whose
@@ -85,17 +88,56 @@ __device__ __forceinline__ void stage_store_tile(const uint8_t* s, void* out, in
 /* The container width of B-bit elements. */
 __host__ __device__ constexpr int container_of(int B) { return B <= 8 ? 1 : (B <= 16 ? 2 : 4); }
 
+/* A full, 16-byte aligned tile's 2*CB chunks of the lane. */
+template <int CB>
+__device__ __forceinline__ void load_chunks(const void* in, int64_t e0, int lane, uint4* v) {
+    const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(in) + e0 * CB);
+#pragma unroll
+    for (int k = 0; k < 2 * CB; ++k) v[k] = __ldcs(src + lane + 32 * k);
+}
+
+/* Whether a transpose kernel loads the next tile ahead: for 2- and 1-byte
+ * containers.  Measured at 2^28 elements on 2-byte ones: 1-3% faster for
+ * 1/4/4 and 1/5/7, pack and unpack.  For 4-byte containers (twice the
+ * registers) it lost as often as it won (1/8/15, 1/8/23: +-2-3%), so they
+ * keep one tile in flight per warp. */
+__host__ __device__ constexpr bool tp_prefetch(int CB) { return CB <= 2; }
+
+/* Full, aligned tiles: each warp loads the next tile's chunks before it
+ * transposes and stores the current one, so that two tiles' loads are in
+ * flight per warp (tp_prefetch).  Other tiles (the ragged last one, the
+ * padding, an unaligned array) are staged element by element when their
+ * turn comes. */
 template <int B>
 __global__ void __launch_bounds__(32 * TP_WARPS) pack_kernel(const void* __restrict__ in, int64_t n,
                                                              uint32_t* __restrict__ out, int64_t S, bool vec) {
     constexpr int CB = container_of(B);
+    constexpr bool PF = tp_prefetch(CB);
     __shared__ __align__(16) uint8_t sm[TP_WARPS][1024 * CB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t* s = sm[warp];
     const int rho = stage_rho<CB>(lane);
     const int64_t ntiles = S / 32;
-    for (int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * TP_WARPS) {
-        stage_load_tile<CB>(s, in, tile * 1024, n, vec, lane);
+    const int64_t stride = (int64_t)gridDim.x * TP_WARPS;
+    int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp;
+    bool cur_full = PF && vec && tile < ntiles && tile * 1024 + 1024 <= n;
+    uint4 cur[2 * CB];
+    if (cur_full) load_chunks<CB>(in, tile * 1024, lane, cur);
+    for (; tile < ntiles; tile += stride) {
+        if constexpr (!PF) {
+            cur_full = vec && tile * 1024 + 1024 <= n;
+            if (cur_full) load_chunks<CB>(in, tile * 1024, lane, cur);
+        }
+        const int64_t nt = tile + stride;
+        const bool nxt_full = PF && vec && nt < ntiles && nt * 1024 + 1024 <= n;
+        uint4 nxt[2 * CB];
+        if (nxt_full) load_chunks<CB>(in, nt * 1024, lane, nxt);
+        if (cur_full) {
+#pragma unroll
+            for (int k = 0; k < 2 * CB; ++k) reinterpret_cast<uint4*>(s)[lane + 32 * k] = cur[k];
+        } else {
+            stage_load_tile<CB>(s, in, tile * 1024, n, false, lane);
+        }
         __syncwarp();
         uint32_t w[8 * CB], x[8 * CB];
         stage_read_column<CB>(s, lane, w);
@@ -104,28 +146,59 @@ __global__ void __launch_bounds__(32 * TP_WARPS) pack_kernel(const void* __restr
         uint32_t* o = out + tile * 32 + lane;
 #pragma unroll
         for (int b = 0; b < B; ++b) __stcs(o + b * S, rotl32(x[b], rho));
+        if constexpr (PF) {
+            if (nxt_full) {
+#pragma unroll
+                for (int k = 0; k < 2 * CB; ++k) cur[k] = nxt[k];
+            }
+            cur_full = nxt_full;
+        }
     }
 }
 
+/* The lane's B plane words of a tile's column. */
+template <int B>
+__device__ __forceinline__ void load_planes(const uint32_t* __restrict__ in, int64_t S, int64_t tile, int lane,
+                                            uint32_t* v) {
+    const uint32_t* src = in + tile * 32 + lane;
+#pragma unroll
+    for (int b = 0; b < B; ++b) v[b] = __ldcs(src + b * S);
+}
+
+/* Each warp loads the next tile's plane words before it transposes and
+ * stores the current one, so that two tiles' loads are in flight per warp
+ * (tp_prefetch). */
 template <int B>
 __global__ void __launch_bounds__(32 * TP_WARPS) unpack_kernel(const uint32_t* __restrict__ in, int64_t S,
                                                                void* __restrict__ out, int64_t n, bool vec) {
     constexpr int CB = container_of(B);
+    constexpr bool PF = tp_prefetch(CB);
     __shared__ __align__(16) uint8_t sm[TP_WARPS][1024 * CB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t* s = sm[warp];
     const int rho = stage_rho<CB>(lane);
     const int64_t ntiles = (n + 1023) / 1024;
-    for (int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * TP_WARPS) {
-        const uint32_t* src = in + tile * 32 + lane;
+    const int64_t stride = (int64_t)gridDim.x * TP_WARPS;
+    int64_t tile = (int64_t)blockIdx.x * TP_WARPS + warp;
+    uint32_t cur[B];
+    if (PF && tile < ntiles) load_planes<B>(in, S, tile, lane, cur);
+    for (; tile < ntiles; tile += stride) {
+        if constexpr (!PF) load_planes<B>(in, S, tile, lane, cur);
+        const bool more = PF && tile + stride < ntiles;
+        uint32_t nxt[B];
+        if (more) load_planes<B>(in, S, tile + stride, lane, nxt);
         uint32_t x[8 * CB], w[8 * CB];
 #pragma unroll
-        for (int b = 0; b < 8 * CB; ++b) x[b] = (b < B) ? rotr32(__ldcs(src + b * S), rho) : 0u;
+        for (int b = 0; b < 8 * CB; ++b) x[b] = (b < B) ? rotr32(cur[(b < B) ? b : 0], rho) : 0u;
         planes_to_rows<CB>(x, w);
         stage_write_column<CB>(s, lane, w);
         __syncwarp();
         stage_store_tile<CB>(s, out, tile * 1024, n, vec, lane);
         __syncwarp();   /* the next tile may overwrite the staging area */
+        if (more) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) cur[b] = nxt[b];
+        }
     }
 }
 
