@@ -909,7 +909,7 @@ def run_e2e(bs, torch, n, rank, args):
             "host_link": link,
             "path": "pinned host -> bsfp_pipeline_submit per format, one bsfp_pipeline_wait per step (chunks "
                     "of %d over %d streams: H2D, bsfp_pack, bsfp_add + bsfp_mul, bsfp_unpack, D2H) -> pinned host"
-                    % (args.e2e_chunk or (1 << 23), args.e2e_depth or 4)}
+                    % (args.e2e_chunk or (1 << 24), args.e2e_depth or 4)}
 
 
 def main(argv=None):

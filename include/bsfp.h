@@ -301,7 +301,7 @@ typedef struct bsfp_pipeline_st* bsfp_pipeline;
 
 #define BSFP_PIPE_MAX_OPS 4
 
-/* chunk: elements per chunk, a multiple of 1024 in [1024, 2^30] (0 = 2^23);
+/* chunk: elements per chunk, a multiple of 1024 in [1024, 2^30] (0 = 2^24);
  * depth: streams, 1..16 (0 = 4).  Created on the current device. */
 bsfp_status bsfp_pipeline_create(int64_t chunk, int32_t depth, bsfp_pipeline* out);
 /* outs[q][i] = ops[q](a[i], b[i] [, c[i]]) for i < n, q < nops (1..4; c is

@@ -123,7 +123,7 @@ extern "C" {
 bsfp_status bsfp_pipeline_create(int64_t chunk, int32_t depth, bsfp_pipeline* out) {
     if (!out) return BSFP_ERR_NULL;
     *out = nullptr;
-    if (chunk == 0) chunk = 1 << 23;
+    if (chunk == 0) chunk = 1 << 24;
     if (depth == 0) depth = 4;
     if (chunk < 1024 || chunk > (1LL << 30) || chunk % 1024 != 0 || depth < 1 || depth > 16) return BSFP_ERR_SIZE;
     bsfp_pipeline_st* P = new bsfp_pipeline_st();
