@@ -359,3 +359,36 @@ def test_server_options_are_checked_before_anything_is_allocated(field, value):
 def test_server_bulk_submit_arguments():
     L = _binding._lib()
     assert L.bsfp_server_submit_n(None, None, 1, None, None) == bs.ERR_NULL
+
+
+def test_stream_shapes_fit_and_load_the_schedulers_evenly():
+    """Every compiled streamed kernel (all formats, ops and modes): a tile is
+    a whole number of consumer warps' columns (64 each), the ring of NIN
+    planes x tile x stages fits the 227 KB one block may use, and the
+    consumer count is one that spreads evenly over the SM's four schedulers
+    (warp index mod 4): never 9 or 10, which measured 7-13% slower than 8
+    on the logic-bound multipliers."""
+    seen = set()
+    for E in range(2, 9):
+        for M in range(1, 24):
+            if 1 + E + M > 32:
+                continue
+            B = 1 + E + M
+            for rnd in range(4):
+                f = bs.Format(E, M, rnd)
+                for op in ("add", "mul", "fma2", "div"):
+                    try:
+                        if bs.VARIANT_STREAMED not in bs.bsfp_variants_compiled(f, op):
+                            continue
+                    except bs.BsfpError:
+                        continue
+                    tw, stages = bs.bsfp_stream_shape(f, op)
+                    assert tw % 64 == 0 and stages >= 2, (E, M, rnd, op, tw, stages)
+                    nc = tw // 64
+                    nin = 3 * B if (op == "fma2" and B <= 13) else 2 * B
+                    assert nin * tw * 4 * stages + 256 <= 232448, (E, M, rnd, op, tw, stages)
+                    assert nc not in (9, 10) and 8 <= nc <= 15, (E, M, rnd, op, nc)
+                    seen.add((op, nc, stages))
+    # every op class has a streamed kernel somewhere, in several shapes
+    assert {op for op, _, _ in seen} == {"add", "mul", "fma2", "div"}
+    assert len(seen) >= 8
